@@ -1,0 +1,409 @@
+"""Benchmark: photon histories/s + ML-EM iterations/s on the 128^3 torso.
+
+One step = the whole hot path on one acquisition: transport + tally of the
+histories into the system matrix (CSR + CSC), start image, and the ML-EM
+iterations.  The phantom, geometry tables and projections are resident in
+HBM before the timed region (a transport plan); L2 is flushed between timed
+steps.  Printed as one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the FP64 C transport + tally) on the
+host cores on a bounded sample of the same workload.  With N > 1 (torchrun)
+every rank reconstructs its own acquisition (its own seed): independent
+problems, no collective on the data path, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2105_13324_gb300 import phantoms as P  # noqa: E402
+
+METRIC = "photon histories/s + MLEM iter/s (128³, 120 views) vs oracle and HBM roofline"
+UNIT = "photon histories/s"
+
+# Algorithmic work model of one history (lane operations; an FMA counts as
+# one): Philox4x32-10 is 10 rounds x 10 integer ops per 4 words, plus the
+# conversion to a uniform; a Woodcock flight is a log, the move, the box
+# test, the voxel index and address, the attenuation and the real/virtual
+# test; an accepted scatter includes the cross-section update at the new
+# energy, ~2.2 rejection trials, the azimuth and the rotation; emission is
+# the start point and direction.
+OPS_PER_DRAW = 27.0
+OPS_PER_FLIGHT = 32.0
+OPS_PER_SCATTER = 90.0
+OPS_PER_EMISSION = 30.0
+ALU_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _maxreduce(value: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Rank r reconstructs its own acquisition: seed base + 7919 r."""
+    return base_seed + 7919 * rank
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, target_s: float = 12.0, max_histories: int = 400_000_000):
+    """Times the oracle (FP64 C transport + tally + count matrix) on the host
+    cores over the first H_s histories of the workload, H_s chosen so that
+    the run takes about target_s seconds."""
+    import oracle
+    pr = oracle.Problem(w.phantom, w.geometry)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    cal = 2_000_000
+    oracle.run(pr, w.seed, 0, cal, threads)
+    rate = cal / max(time.perf_counter() - t0, 1e-6)
+    hs = int(min(max_histories, max(cal, rate * target_s)))
+    t0 = time.perf_counter()
+    rows, cols, fates = oracle.run(pr, w.seed, 0, hs, threads)
+    c = oracle.system_counts(rows, cols, pr.n_rows, pr.n_voxels)
+    dt = time.perf_counter() - t0
+    a = oracle.system_matrix(c, oracle.histories_per_voxel(pr.n_voxels, 0, hs))
+    y = np.asarray(a @ w.phantom.activity.ravel().astype(np.float64))
+    x = oracle.mlem_init(a, y)
+    t1 = time.perf_counter()
+    n_it = 3
+    oracle.mlem(a, y, x, n_it)
+    mlem_s = (time.perf_counter() - t1) / n_it
+    return {"value": hs / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"histories 0..{hs - 1} of the {w.name} workload (FP64 C transport + tally + count matrix, "
+                      f"{threads} threads), {dt:.1f} s; ML-EM float64 on that sample's matrix (nnz {c.nnz}): "
+                      f"{1.0 / mlem_s:.2f} iter/s",
+            "histories": hs, "seconds": dt, "mlem_iter_per_s": 1.0 / mlem_s, "mlem_nnz": int(c.nnz)}
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per = max(3.0, min(15.0, 150.0 / max(args.steps + args.warmup, 1)))
+    import oracle
+    oracle.build()
+    pr = oracle.Problem(w.phantom, w.geometry)
+    threads = os.cpu_count() or 1
+    cal = 2_000_000
+    t0 = time.perf_counter()
+    oracle.run(pr, w.seed, 0, cal, threads)
+    rate = cal / max(time.perf_counter() - t0, 1e-6)
+    hs = int(max(cal, rate * per))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rows, cols, _ = oracle.run(pr, w.seed, i * hs, hs, threads)
+        oracle.system_counts(rows, cols, pr.n_rows, pr.n_voxels)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    value = hs * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "histories_per_step": hs,
+                                            "note": "CPU oracle on a bounded history sample per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{hs} histories per step of the {w.name} workload, transport + tally"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, w):
+    import torch
+
+    from paper_2105_13324_gb300 import build as B
+    from paper_2105_13324_gb300 import mcspect as mc
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mc.load(B.build())
+    H = int(args.histories or w.n_histories)
+    n_iter = int(args.mlem_iters or w.mlem_iters)
+    seed = shard_seed(w.seed, rank)
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM: plan (map + tables) and the projections y
+    plan = mc.Plan(w.phantom, w.geometry, "fp32")
+    truth = plan.build(0, H, seed + 1000)
+    act = torch.as_tensor(w.phantom.activity.ravel()).to(dev)
+    M, N = truth.shape
+    ybar = torch.zeros(M, dtype=torch.float32, device=dev)
+    mc.mc_project(truth, act, ybar)
+    y_host = P.poisson_counts(ybar.cpu().numpy(), w.total_counts, w.noise_seed + rank)
+    truth.free()
+    y = torch.as_tensor(y_host).to(dev)
+    x = torch.zeros(N, dtype=torch.float32, device=dev)
+    flush = torch.empty(int(args.flush_mb) * (1 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        s = plan.build(0, H, seed)
+        mc.mc_mlem_init(s, y, x)
+        mc.mlem_iterate(s, y, x, n_iter)
+        return s
+
+    for _ in range(args.warmup):
+        step().free()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    l0 = mc.mc_kernel_launches()
+    t_transport, t_assembly, infos = [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        s = step()
+        ev[k][1].record(stream)
+        inf = s.info()
+        t_transport.append(inf["build_ms_transport"])
+        t_assembly.append(inf["build_ms_assembly"])
+        infos.append(inf)
+        if k == args.steps - 1:
+            last = s
+        else:
+            s.free()
+    torch.cuda.synchronize()
+    launches = mc.mc_kernel_launches() - l0
+    _barrier(ws)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = _maxreduce(float(np.mean(step_ms)), ws, dev)
+    value = ws * H / (ms * 1e-3)
+
+    # ML-EM alone on the last system: iterations/s and the SpMV roofline
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    mlem_ms = []
+    for _ in range(reps):
+        flush.zero_()
+        mc.mc_mlem_init(last, y, x)
+        e0.record(stream)
+        mc.mlem_iterate(last, y, x, n_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mlem_ms.append(e0.elapsed_time(e1))
+    it_ms = float(np.median(mlem_ms)) / n_iter
+    inf = infos[-1]
+    nnz = inf["nnz"]
+    rp, _, _ = last.export_csr()
+    cp, _, _, _ = last.export_csc()
+    m_nz = int(np.count_nonzero(np.diff(rp)))
+    n_nz = int(np.count_nonzero(np.diff(cp)))
+    mlem_bytes = (2 * nnz * (4 + 4) + 4 * (M + 1) + 4 * (N + 1)
+                  + 4 * (n_nz + m_nz + 2 * m_nz + n_nz + 2 * n_nz))
+    hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+
+    # transport roofline (lane-op issue bound), work counted from an FP64
+    # trace of a history sample of this workload
+    rec = mc.mc_trace_histories(w.phantom, w.geometry, seed, 0, 200_000, precision="fp64")
+    esc = (rec["fate"] == 2).astype(np.float64)
+    flights = rec["n_virtual"] + rec["n_real"] + esc
+    ops = (OPS_PER_DRAW * rec["n_draws"] + OPS_PER_FLIGHT * flights + OPS_PER_SCATTER * rec["n_compton"]
+           + OPS_PER_EMISSION).mean()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * ALU_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12  # T lane-ops/s
+    t_tr = float(np.mean(t_transport))
+    achieved = ops * H / (t_tr * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers
+    y_pin = torch.as_tensor(y_host).pin_memory()
+    x_pin = torch.empty(N, dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+
+    def e2e_step():
+        s = mc.mc_build_system(w.phantom, w.geometry, H, seed)
+        y_dev.copy_(y_pin, non_blocking=True)
+        mc.mc_mlem_init(s, y_dev, x)
+        mc.mlem_iterate(s, y_dev, x, n_iter)
+        x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        s.free()
+        return float(x_pin[0])
+
+    e2e_step()
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_val = ws * H / (_maxreduce(float(np.mean(e2e_ms)), ws, dev) * 1e-3)
+    n_mat = len(w.phantom.rho)
+    V = w.geometry.n_views
+    h2d = w.phantom.material.size + 3 * 8 * n_mat + 2 * V * (8 + 4) + 3 * n_mat * (8 + 4) + 4 * M
+    d2h = 4 * N + 5 * 8 + 4 + 4 + 4
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, target_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.phantom.shape), "voxel_mm": w.phantom.voxel_mm,
+                       "views": V, "bins": [w.geometry.n_bins_v, w.geometry.n_bins_u], "histories_per_step": H,
+                       "mlem_iters": n_iter, "matrix": "CSR+CSC u32 counts, f32 values",
+                       "l2": f"flushed ({args.flush_mb} MB write) between timed steps",
+                       "parallelism": f"{ws} independent acquisitions" if ws > 1 else "1 GPU"},
+            "mlem_iter_per_s": 1e3 / it_ms,
+            "transport_histories_per_s": H / (t_tr * 1e-3),
+            "step_breakdown_ms": {"transport": t_tr, "assembly": float(np.mean(t_assembly)),
+                                  "mlem": it_ms * n_iter},
+            "matrix": {"rows": M, "cols": N, "nnz": nnz, "events": inf["n_events"], "fates": inf["fates"],
+                       "max_count": inf["max_count"]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
+                         "frac": achieved / alu_peak, "traffic": None, "kernel": "transport_kernel<float>",
+                         "ops_per_history": ops,
+                         "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {sm_max_mhz:.0f} MHz"},
+            "roofline_mlem": {"bound": "hbm", "achieved": mlem_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm_gbs,
+                              "unit": "GB/s", "frac": mlem_bytes / (it_ms * 1e-3) / 1e9 / hbm_gbs,
+                              "traffic": None, "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
+                              "note": "matrix of this workload fits in L2"},
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    last.free()
+    plan.free()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="torso128")
+    ap.add_argument("--histories", type=int, default=None, help="override histories per step")
+    ap.add_argument("--mlem-iters", type=int, default=None)
+    ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    w = P.workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * mcspect.h -- C ABI of the GB300 Monte Carlo SPECT library (libmcspect.so).
+ *
+ * The library estimates the SPECT system matrix of the inverse Monte Carlo
+ * model, Eq. (IMC) of Sec. 5.1,
+ *     P_j = sum_i T_ij S_i,
+ * by analog photon transport on the GPU, and reconstructs the source S with
+ * the ML-EM update of Eq. (MLEM), Sec. 5.1.  Matrix rows j are detector bins
+ * (view-major, then axial bin, then transaxial bin); columns i (called v
+ * below) are voxels (x fastest).
+ *
+ * Conventions for every entry point:
+ *   - returns MC_OK (0) or a negative MC_E* code; no exception crosses the
+ *     ABI; mc_last_error() gives a message for the calling thread;
+ *   - "_host" pointers are host memory, "_dev" pointers are device memory of
+ *     the current CUDA device; the caller owns and frees every buffer it
+ *     passes; an mc_system is owned by the library until mc_system_free;
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry
+ *     points that take device buffers only enqueue work on `stream` and
+ *     return without waiting unless stated otherwise;
+ *   - an mc_system is not thread-safe: calls on one system must not overlap
+ *     on the GPU (they share the system's work vectors).
+ */
+#ifndef MCSPECT_H
+#define MCSPECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* exported from libmcspect.so */
+#if defined(__GNUC__)
+#define MC_API __attribute__((visibility("default")))
+#else
+#define MC_API
+#endif
+
+#define MC_OK 0
+#define MC_EINVAL (-1)   /* bad argument (null pointer, size, range) */
+#define MC_ENOMEM (-2)   /* device or host allocation failed */
+#define MC_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+#define MC_ETIMEOUT (-4) /* a bounded device wait ran out */
+#define MC_EFORMAT (-5)  /* malformed serialized matrix */
+
+/* transport precision */
+#define MC_FP32 0 /* production: float arithmetic, 23-bit uniforms */
+#define MC_FP64 1 /* verification: double arithmetic, 32-bit uniforms */
+
+/* storage type of matrix values used by the projectors */
+#define MC_VAL_F32 0
+#define MC_VAL_F16 1
+#define MC_VAL_BF16 2
+
+/* history fates */
+#define MC_FATE_ABSORBED 0
+#define MC_FATE_BELOW_WINDOW 1
+#define MC_FATE_ESCAPE 2
+#define MC_FATE_CAP 3
+
+/* Voxelised attenuation map (Sec. 3: patient size, shape, composition).
+ * Grid centred on the origin; voxel (i,j,k) covers
+ * [i h - nx h/2, (i+1) h - nx h/2) x ... ; material index per voxel into a
+ * table of at most 256 materials.  mu(m,E) = 0.1 rho_m (N_A (Z/A)_m
+ * sigma_KN(E) + photo_k Z_eff,m^4 / E^3) per mm, E in keV. */
+typedef struct mc_phantom {
+  int32_t nx, ny, nz;
+  double voxel_mm;
+  const uint8_t *material_host; /* nz*ny*nx, x fastest */
+  int32_t n_materials;          /* 1..256 */
+  const double *rho_host;       /* g/cm^3, [n_materials] */
+  const double *z_over_a_host;  /* [n_materials] */
+  const double *z_eff_host;     /* [n_materials] */
+} mc_phantom;
+
+/* Acquisition (Sec. 3): one parallel-hole collimated head per view; view k
+ * at angle theta_k = (start_deg + k (arc_deg / n_views)) degrees, outward
+ * normal (cos, sin, 0), transaxial axis (-sin, cos, 0), axial axis z.  The
+ * collimator front face is at radius_mm from the axis (it must clear the
+ * grid), the crystal at radius_mm + hole_len_mm.  Detection window
+ * [(1 - window_frac/2) e0_kev, (1 + window_frac/2) e0_kev]. */
+typedef struct mc_geometry {
+  int32_t n_views;
+  double start_deg, arc_deg;
+  int32_t n_bins_u, n_bins_v; /* transaxial, axial */
+  double bin_mm;
+  double radius_mm;
+  double hole_len_mm, hole_diam_mm;
+  double fwhm_mm; /* Gaussian intrinsic blur */
+  double e0_kev, window_frac;
+  double photo_k;
+  int32_t precision; /* MC_FP32 or MC_FP64 */
+} mc_geometry;
+
+typedef struct mc_system mc_system; /* opaque, device resident */
+
+typedef struct mc_system_info {
+  int64_t n_rows;        /* M = n_views * n_bins_v * n_bins_u */
+  int64_t n_cols;        /* N = voxels */
+  int64_t nnz;           /* distinct (row, col) pairs with a count */
+  int64_t n_events;      /* detections tallied */
+  uint64_t first_history, n_histories;
+  uint64_t fates[4];     /* ABSORBED, BELOW_WINDOW, ESCAPE, CAP */
+  uint32_t max_count;    /* largest C_jv */
+  int32_t value_type;    /* MC_VAL_* used by the projectors */
+  double build_ms_transport, build_ms_assembly; /* device time of the last build */
+} mc_system_info;
+
+/* Per-history trace (verification): 48 bytes, this exact layout. */
+typedef struct mc_history_record {
+  uint8_t fate, n_events; /* n_events saturates at 255 */
+  uint16_t pad;
+  uint32_t n_virtual, n_real, n_compton, n_draws;
+  uint32_t pad2;
+  double e_final_kev;
+  int32_t event_row[4]; /* first four detections' rows */
+} mc_history_record;
+
+/* Transport + tally (Sec. 2; Sec. 5.1, T_ij estimated by Monte Carlo).
+ * Runs histories 0 .. n_histories-1 of the stream keyed by `seed`; history h
+ * starts in voxel h mod N.  The result holds C_jv (integer counts), n_v
+ * (histories started in voxel v) and the matrix A = C diag(1/n_v) used by
+ * the projectors, in CSR and CSC form.  Host inputs are copied; the call
+ * returns after the matrix is built (it synchronises `stream`).
+ * Errors: MC_EINVAL (bad sizes, front face inside the grid, n_histories 0),
+ * MC_ENOMEM, MC_ECUDA. */
+MC_API int mc_build_system(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t n_histories,
+                    uint64_t seed, void *stream, mc_system **out);
+
+/* A phantom + geometry made resident on the device (map, view table,
+ * attenuation coefficients), for repeated builds without host traffic.
+ * Host inputs are copied; the call synchronises `stream`.
+ * Errors: as mc_build_system. */
+typedef struct mc_plan mc_plan;
+MC_API int mc_plan_create(const mc_phantom *phantom, const mc_geometry *geometry, void *stream, mc_plan **out);
+
+/* Transport + tally of histories first .. first+count-1 from a plan; same
+ * result as mc_build_system_range with the plan's inputs. */
+MC_API int mc_plan_build(mc_plan *plan, uint64_t first, uint64_t count, uint64_t seed, void *stream,
+                         mc_system **out);
+
+/* Release a plan (NULL is accepted). */
+MC_API int mc_plan_free(mc_plan *plan);
+
+/* As mc_build_system for histories first .. first+count-1 only (chunked or
+ * resumed runs): the counts and n_v of disjoint ranges add up exactly to
+ * those of their union. */
+MC_API int mc_build_system_range(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t first,
+                          uint64_t count, uint64_t seed, void *stream, mc_system **out);
+
+/* Matrix from an explicit event list (row j, column v), e.g. tallies made
+ * elsewhere; n_v is that of the history range [first, first+count).
+ * Duplicates add.  Errors: MC_EINVAL for an index out of range. */
+MC_API int mc_system_from_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_host, const int32_t *cols_host,
+                          int64_t n_events, uint64_t first, uint64_t count, void *stream, mc_system **out);
+
+/* Release a system and its device memory (NULL is accepted). */
+MC_API int mc_system_free(mc_system *sys);
+
+MC_API int mc_system_info_get(const mc_system *sys, mc_system_info *info);
+
+/* Copy the count matrix to the host in CSC form: col_ptr[n_cols+1],
+ * row_idx[nnz] (ascending within a column), counts[nnz]; n_v[n_cols].
+ * Any pointer may be NULL to skip that array.  Synchronises `stream`. */
+MC_API int mc_system_export_csc(const mc_system *sys, int64_t *col_ptr_host, int32_t *row_idx_host, uint32_t *counts_host,
+                         uint32_t *n_v_host, void *stream);
+
+/* Same in CSR form: row_ptr[n_rows+1], col_idx[nnz] ascending within a row. */
+MC_API int mc_system_export_csr(const mc_system *sys, int64_t *row_ptr_host, int32_t *col_idx_host, uint32_t *counts_host,
+                         void *stream);
+
+/* Storage type of the values the projectors read (MC_VAL_F32 default;
+ * MC_VAL_F16 / MC_VAL_BF16 store the integer counts C_jv, exact up to 2048 /
+ * 256, accumulation stays FP32).  Returns MC_EINVAL if a count is not exact
+ * in the requested type unless allow_rounding is non-zero. */
+MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t allow_rounding);
+
+/* Forward projection q = A x (Eq. (IMC)): x_dev[N], q_dev[M], float. */
+MC_API int mc_project(const mc_system *sys, const float *x_dev, float *q_dev, void *stream);
+
+/* Back-projection b = A^T r: r_dev[M], b_dev[N], float. */
+MC_API int mc_backproject(const mc_system *sys, const float *r_dev, float *b_dev, void *stream);
+
+/* Sensitivity s_v = sum_j A_jv (the normaliser of Eq. (MLEM)), FP64:
+ * s_dev[N] double. */
+MC_API int mc_sensitivity(const mc_system *sys, double *s_dev, void *stream);
+
+/* Uniform start image: x_v = sum(y) / sum(s) where s_v > 0, else 0. */
+MC_API int mc_mlem_init(mc_system *sys, const float *y_dev, float *x_dev, void *stream);
+
+/* n_iter ML-EM updates of Eq. (MLEM), in place on x_dev[N]:
+ *   x_v <- x_v / s_v * sum_j A_jv y_j / (A x)_j,
+ * with y_j / (A x)_j taken as 0 where (A x)_j = 0 and x_v = 0 where s_v = 0.
+ * If loglik_host is not NULL it receives n_iter values
+ * L(x^k) = sum_j y_j ln q_j - q_j (FP64; bins with y_j = 0 add -q_j) for
+ * the iterates before each update, and the call synchronises `stream`. */
+MC_API int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter, double *loglik_host,
+                 void *stream);
+
+/* Verification: per-history trace records of histories first ..
+ * first+count-1 (records written to out_host[count]).  Synchronises. */
+MC_API int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,
+                       uint64_t count, mc_history_record *out_host);
+
+/* Verification of the Compton sampler (Sec. 3: a scatter lowers the energy
+ * and changes the direction): sample i uses history i's stream; writes
+ * cos(theta) and E'/E.  precision MC_FP32 or MC_FP64.  Synchronises. */
+MC_API int mc_debug_kn(double e_kev, int32_t precision, uint64_t seed, uint64_t n, double *cos_out_host,
+                double *eps_out_host);
+
+/* Verification of Woodcock tracking: n photons of energy e_kev start at
+ * p0_host[3] with direction d_host[3] (photon i uses history i's stream);
+ * *through_host = how many leave the grid without a real collision. */
+MC_API int mc_debug_beam(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t n,
+                  const double *p0_host, const double *d_host, double e_kev, uint64_t *through_host);
+
+/* Number of kernels this library has launched in this process (all
+ * devices, all threads); for launch accounting in benchmarks. */
+MC_API uint64_t mc_kernel_launches(void);
+
+/* Message of the last error on this thread ("" if none). */
+MC_API const char *mc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCSPECT_H */

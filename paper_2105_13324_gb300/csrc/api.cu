@@ -1,0 +1,596 @@
+// api.cu -- the extern "C" entry points of libmcspect.so (include/mcspect.h):
+// argument checks, the build pipeline (transport -> assembly -> values) and
+// the projector / ML-EM calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mcs {
+
+static thread_local std::string g_error;
+
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+}
+
+void clear_error() { g_error.clear(); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::vector<int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+int launch_transport_f32(const TransportSetup &ts, cudaStream_t s);
+int launch_transport_f64(const TransportSetup &ts, cudaStream_t s);
+int launch_debug_kn_f32(double e, uint64_t seed, uint64_t n, double *c, double *p, cudaStream_t s);
+int launch_debug_kn_f64(double e, uint64_t seed, uint64_t n, double *c, double *p, cudaStream_t s);
+int launch_debug_beam_f32(const TransportSetup &ts, uint64_t n, const double p0[3], const double d[3], double e,
+                          unsigned long long *t, cudaStream_t s);
+int launch_debug_beam_f64(const TransportSetup &ts, uint64_t n, const double p0[3], const double d[3], double e,
+                          unsigned long long *t, cudaStream_t s);
+
+int project(const mc_system *sys, const float *x, float *q, cudaStream_t s);
+int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s);
+int sensitivity(const mc_system *sys, double *out, cudaStream_t s);
+int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s);
+int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll, cudaStream_t s);
+int forward_blocks(const mc_system *sys);
+void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf);
+
+static constexpr double kPiHost = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+static int check_phantom(const mc_phantom *ph) {
+  if (!ph) { set_error("phantom is NULL"); return MC_EINVAL; }
+  if (ph->nx < 1 || ph->ny < 1 || ph->nz < 1) { set_error("grid dimensions must be positive"); return MC_EINVAL; }
+  const uint64_t nv = (uint64_t)ph->nx * ph->ny * ph->nz;
+  if (nv >= (1ull << 31)) { set_error("grid of %llu voxels exceeds 2^31", (unsigned long long)nv); return MC_EINVAL; }
+  if (!(ph->voxel_mm > 0.0) || !std::isfinite(ph->voxel_mm)) { set_error("voxel_mm must be positive"); return MC_EINVAL; }
+  if (!ph->material_host || !ph->rho_host || !ph->z_over_a_host || !ph->z_eff_host) {
+    set_error("phantom arrays must not be NULL");
+    return MC_EINVAL;
+  }
+  if (ph->n_materials < 1 || ph->n_materials > 256) { set_error("n_materials must be in 1..256"); return MC_EINVAL; }
+  for (int m = 0; m < ph->n_materials; ++m) {
+    if (!(ph->rho_host[m] >= 0.0) || !(ph->z_over_a_host[m] >= 0.0) || !(ph->z_eff_host[m] >= 0.0) ||
+        !std::isfinite(ph->rho_host[m]) || !std::isfinite(ph->z_over_a_host[m]) || !std::isfinite(ph->z_eff_host[m])) {
+      set_error("material %d has a negative or non-finite property", m);
+      return MC_EINVAL;
+    }
+  }
+  for (uint64_t i = 0; i < nv; ++i) {
+    if (ph->material_host[i] >= ph->n_materials) {
+      set_error("voxel %llu has material %d outside the table", (unsigned long long)i, (int)ph->material_host[i]);
+      return MC_EINVAL;
+    }
+  }
+  return MC_OK;
+}
+
+static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
+  if (!g) { set_error("geometry is NULL"); return MC_EINVAL; }
+  if (g->n_views < 1 || g->n_bins_u < 1 || g->n_bins_v < 1) { set_error("views and bins must be positive"); return MC_EINVAL; }
+  const uint64_t m = (uint64_t)g->n_views * g->n_bins_u * g->n_bins_v;
+  if (m >= (1ull << 31)) { set_error("%llu detector rows exceed 2^31", (unsigned long long)m); return MC_EINVAL; }
+  const double vals[] = {g->start_deg, g->arc_deg, g->bin_mm, g->radius_mm, g->hole_len_mm, g->hole_diam_mm,
+                         g->fwhm_mm, g->e0_kev, g->window_frac, g->photo_k};
+  for (double v : vals)
+    if (!std::isfinite(v)) { set_error("geometry has a non-finite value"); return MC_EINVAL; }
+  if (!(g->bin_mm > 0) || !(g->hole_len_mm > 0) || !(g->hole_diam_mm > 0) || !(g->fwhm_mm >= 0) || !(g->e0_kev > 0) ||
+      !(g->window_frac > 0 && g->window_frac < 2) || !(g->photo_k >= 0) || !(g->arc_deg > 0)) {
+    set_error("geometry values out of range");
+    return MC_EINVAL;
+  }
+  if (g->precision != MC_FP32 && g->precision != MC_FP64) { set_error("precision must be MC_FP32 or MC_FP64"); return MC_EINVAL; }
+  if (ph) {
+    const double hx = 0.5 * ph->nx * ph->voxel_mm, hy = 0.5 * ph->ny * ph->voxel_mm;
+    if (!(g->radius_mm > std::sqrt(hx * hx + hy * hy))) {
+      set_error("collimator front face (radius %.3f mm) must clear the grid (half-diagonal %.3f mm)", g->radius_mm,
+                std::sqrt(hx * hx + hy * hy));
+      return MC_EINVAL;
+    }
+  }
+  return MC_OK;
+}
+
+}  // namespace mcs
+
+// A phantom + geometry resident on the device: the map, the view table and
+// the attenuation coefficients, ready for any number of builds.
+struct mc_plan {
+  mcs::TransportSetup ts;
+  mcs::DevBuf material, views_d, views_f, coef_d, coef_f;
+};
+
+namespace mcs {
+
+static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t s, mc_plan &pl) {
+  TransportSetup &ts = pl.ts;
+  std::memset(&ts, 0, sizeof(ts));
+  ts.nx = ph->nx; ts.ny = ph->ny; ts.nz = ph->nz;
+  ts.h = ph->voxel_mm;
+  ts.n_mat = ph->n_materials;
+  for (int m = 0; m < ph->n_materials; ++m) {
+    ts.rho[m] = ph->rho_host[m];
+    ts.zoa[m] = ph->z_over_a_host[m];
+    ts.zeff[m] = ph->z_eff_host[m];
+  }
+  ts.n_views = g->n_views; ts.bins_u = g->n_bins_u; ts.bins_v = g->n_bins_v;
+  ts.start_deg = g->start_deg; ts.arc_deg = g->arc_deg; ts.bin_mm = g->bin_mm; ts.radius_mm = g->radius_mm;
+  ts.hole_len = g->hole_len_mm; ts.hole_diam = g->hole_diam_mm; ts.fwhm = g->fwhm_mm;
+  ts.e0 = g->e0_kev; ts.window = g->window_frac; ts.photo_k = g->photo_k;
+  ts.precision = g->precision;
+  const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
+  MCS_TRY(pl.material.alloc(nv, s));
+  MCS_CUDA(cudaMemcpyAsync(pl.material.p, ph->material_host, nv, cudaMemcpyHostToDevice, s));
+  ts.material_dev = pl.material.as<uint8_t>();
+  // view k at theta_k = (start + k (arc / V)) degrees
+  std::vector<double> vd(2 * (size_t)g->n_views);
+  std::vector<float> vf(2 * (size_t)g->n_views);
+  for (int k = 0; k < g->n_views; ++k) {
+    const double th = (g->start_deg + k * (g->arc_deg / g->n_views)) * (kPiHost / 180.0);
+    vd[2 * k] = std::cos(th);
+    vd[2 * k + 1] = std::sin(th);
+    vf[2 * k] = (float)vd[2 * k];
+    vf[2 * k + 1] = (float)vd[2 * k + 1];
+  }
+  std::vector<double> cd;
+  std::vector<float> cf;
+  compute_coefficients(ts, cd, cf);
+  MCS_TRY(pl.views_d.alloc(vd.size() * sizeof(double), s));
+  MCS_TRY(pl.views_f.alloc(vf.size() * sizeof(float), s));
+  MCS_TRY(pl.coef_d.alloc(cd.size() * sizeof(double), s));
+  MCS_TRY(pl.coef_f.alloc(cf.size() * sizeof(float), s));
+  MCS_CUDA(cudaMemcpyAsync(pl.views_d.p, vd.data(), vd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(pl.views_f.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(pl.coef_d.p, cd.data(), cd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(pl.coef_f.p, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaStreamSynchronize(s));  // host vectors die on return
+  ts.view_cs_dev = pl.views_d.as<double>();
+  ts.view_cs_f_dev = pl.views_f.as<float>();
+  ts.coef_d_dev = pl.coef_d.as<double>();
+  ts.coef_f_dev = pl.coef_f.as<float>();
+  return MC_OK;
+}
+
+static int make_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t s, mc_plan **out) {
+  MCS_TRY(check_phantom(ph));
+  MCS_TRY(check_geometry(g, ph));
+  mc_plan *pl = new (std::nothrow) mc_plan();
+  if (!pl) { set_error("out of host memory"); return MC_ENOMEM; }
+  const int rc = prepare_plan(ph, g, s, *pl);
+  if (rc != MC_OK) { delete pl; return rc; }
+  *out = pl;
+  return MC_OK;
+}
+
+static int run_transport(const TransportSetup &ts, cudaStream_t s) {
+  return ts.precision == MC_FP64 ? launch_transport_f64(ts, s) : launch_transport_f32(ts, s);
+}
+
+static int pick_group(double mean_len) {
+  int g = 1;
+  while (g < 32 && g < mean_len) g <<= 1;
+  return g;
+}
+
+// Work vectors and projector values of a freshly assembled system.
+static int finish_system(mc_system *sys, cudaStream_t s) {
+  MCS_TRY(make_values(sys, s));
+  MCS_TRY(sys->xs.alloc((size_t)(sys->n_cols > 0 ? sys->n_cols : 1) * sizeof(float), s));
+  MCS_TRY(sys->r.alloc((size_t)(sys->n_rows > 0 ? sys->n_rows : 1) * sizeof(float), s));
+  sys->spmv_group_fwd = pick_group(sys->n_rows > 0 ? (double)sys->nnz / sys->n_rows : 1.0);
+  sys->spmv_group_bwd = pick_group(sys->n_cols > 0 ? (double)sys->nnz / sys->n_cols : 1.0);
+  const int fb = forward_blocks(sys);
+  MCS_TRY(sys->partials.alloc((size_t)(fb > 0 ? fb : 1) * sizeof(double), s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
+                           mc_system **out) {
+  if (count == 0) { set_error("no histories requested"); return MC_EINVAL; }
+  if (first + count < first) { set_error("history range overflows 64 bits"); return MC_EINVAL; }
+  TransportSetup ts = pl->ts;
+  ts.first = first;
+  ts.count = count;
+  ts.key0 = (uint32_t)seed;
+  ts.key1 = (uint32_t)(seed >> 32);
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete sys; return rc; };
+  sys->n_rows = (int64_t)ts.n_views * ts.bins_u * ts.bins_v;
+  sys->n_cols = (int64_t)ts.nx * ts.ny * ts.nz;
+  sys->first = first;
+  sys->count = count;
+  int rc;
+  // Event capacity: the unattenuated per-view acceptance (d/L)^2/16 per
+  // history, 25 % headroom; rerun with the exact size if it overflows.
+  const double acc = (ts.hole_diam / ts.hole_len) * (ts.hole_diam / ts.hole_len) / 16.0;
+  double est = (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
+  if (est > 4.0e9) est = 4.0e9;
+  unsigned long long cap = (unsigned long long)est;
+  DevBuf events, ctr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+  struct EvGuard { cudaEvent_t a, b, c; ~EvGuard() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); if (c) cudaEventDestroy(c); } } eg{e0, e1, e2};
+  if ((rc = ctr.alloc(5 * sizeof(unsigned long long), s))) return fail(rc);
+  unsigned long long hctr[5];
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
+    if (cudaMemsetAsync(ctr.p, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) {
+      set_error("cudaMemsetAsync failed");
+      return fail(MC_ECUDA);
+    }
+    ts.events = events.as<unsigned long long>();
+    ts.capacity = cap;
+    ts.cursor = ctr.as<unsigned long long>();
+    ts.fates = ctr.as<unsigned long long>() + 1;
+    ts.records = nullptr;
+    cudaEventRecord(e0, s);
+    if ((rc = run_transport(ts, s))) return fail(rc);
+    cudaEventRecord(e1, s);
+    if (cudaMemcpyAsync(hctr, ctr.p, sizeof(hctr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("transport failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return fail(MC_ECUDA);
+    }
+    if (hctr[0] <= cap) break;
+    if (hctr[0] >= 0xFFFFFFFFull) {
+      set_error("%llu events exceed the 2^32 limit of one build; split the history range", hctr[0]);
+      return fail(MC_EINVAL);
+    }
+    cap = hctr[0];
+  }
+  sys->n_events = (int64_t)hctr[0];
+  for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
+  rc = assemble_system(sys, events, sys->n_events, s);
+  if (rc) return fail(rc);
+  if ((rc = finish_system(sys, s))) return fail(rc);
+  cudaEventRecord(e2, s);
+  cudaEventSynchronize(e2);
+  float t1 = 0.f, t2 = 0.f;
+  cudaEventElapsedTime(&t1, e0, e1);
+  cudaEventElapsedTime(&t2, e1, e2);
+  sys->ms_transport = t1;
+  sys->ms_assembly = t2;
+  *out = sys;
+  return MC_OK;
+}
+
+__global__ void events_to_keys_kernel(const int32_t *rows, const int32_t *cols, int64_t n, uint64_t m,
+                                      unsigned long long *keys) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = (unsigned long long)cols[i] * m + (unsigned long long)rows[i];
+}
+
+}  // namespace mcs
+
+using namespace mcs;
+
+#define API_STREAM(x) (static_cast<cudaStream_t>(x))
+
+extern "C" {
+
+const char *mc_last_error(void) { return g_error.c_str(); }
+
+uint64_t mc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int mc_plan_create(const mc_phantom *phantom, const mc_geometry *geometry, void *stream, mc_plan **out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return MC_EINVAL; }
+  *out = nullptr;
+  return make_plan(phantom, geometry, API_STREAM(stream), out);
+}
+
+int mc_plan_build(mc_plan *plan, uint64_t first, uint64_t count, uint64_t seed, void *stream, mc_system **out) {
+  clear_error();
+  if (!plan || !out) { set_error("NULL argument"); return MC_EINVAL; }
+  *out = nullptr;
+  return build_from_plan(plan, first, count, seed, API_STREAM(stream), out);
+}
+
+int mc_plan_free(mc_plan *plan) {
+  clear_error();
+  delete plan;
+  return MC_OK;
+}
+
+int mc_build_system(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t n_histories, uint64_t seed,
+                    void *stream, mc_system **out) {
+  return mc_build_system_range(phantom, geometry, 0, n_histories, seed, stream, out);
+}
+
+int mc_build_system_range(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t first, uint64_t count,
+                          uint64_t seed, void *stream, mc_system **out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return MC_EINVAL; }
+  *out = nullptr;
+  mc_plan *pl = nullptr;
+  MCS_TRY(make_plan(phantom, geometry, API_STREAM(stream), &pl));
+  const int rc = build_from_plan(pl, first, count, seed, API_STREAM(stream), out);
+  delete pl;
+  return rc;
+}
+
+int mc_system_from_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_host, const int32_t *cols_host,
+                          int64_t n_events, uint64_t first, uint64_t count, void *stream, mc_system **out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return MC_EINVAL; }
+  *out = nullptr;
+  if (n_rows < 1 || n_cols < 1 || n_rows >= (1ll << 31) || n_cols >= (1ll << 31) || n_events < 0 ||
+      n_events >= 0xFFFFFFFFll) {
+    set_error("sizes out of range");
+    return MC_EINVAL;
+  }
+  if (n_events > 0 && (!rows_host || !cols_host)) { set_error("event arrays are NULL"); return MC_EINVAL; }
+  for (int64_t i = 0; i < n_events; ++i) {
+    if (rows_host[i] < 0 || rows_host[i] >= n_rows || cols_host[i] < 0 || cols_host[i] >= n_cols) {
+      set_error("event %lld (%d, %d) out of range", (long long)i, rows_host[i], cols_host[i]);
+      return MC_EINVAL;
+    }
+  }
+  cudaStream_t s = API_STREAM(stream);
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete sys; return rc; };
+  sys->n_rows = n_rows;
+  sys->n_cols = n_cols;
+  sys->first = first;
+  sys->count = count;
+  sys->n_events = n_events;
+  DevBuf keys, r, c;
+  int rc;
+  const size_t nb = (size_t)(n_events > 0 ? n_events : 1);
+  if ((rc = keys.alloc(nb * 8, s)) || (rc = r.alloc(nb * 4, s)) || (rc = c.alloc(nb * 4, s))) return fail(rc);
+  if (n_events > 0) {
+    if (cudaMemcpyAsync(r.p, rows_host, n_events * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c.p, cols_host, n_events * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("event upload failed");
+      return fail(MC_ECUDA);
+    }
+    int g = (int)((n_events + 255) / 256);
+    if (g > 65535) g = 65535;
+    count_launch(); events_to_keys_kernel<<<g, 256, 0, s>>>(r.as<int32_t>(), c.as<int32_t>(), n_events, (uint64_t)n_rows,
+                                            keys.as<unsigned long long>());
+    if (cudaGetLastError() != cudaSuccess) { set_error("key kernel launch failed"); return fail(MC_ECUDA); }
+  }
+  r.release();
+  c.release();
+  if ((rc = assemble_system(sys, keys, n_events, s))) return fail(rc);
+  if ((rc = finish_system(sys, s))) return fail(rc);
+  *out = sys;
+  return MC_OK;
+}
+
+int mc_system_free(mc_system *sys) {
+  clear_error();
+  if (!sys) return MC_OK;
+  delete sys;  // DevBufs release their memory on their own streams
+  return MC_OK;
+}
+
+int mc_system_info_get(const mc_system *sys, mc_system_info *info) {
+  clear_error();
+  if (!sys || !info) { set_error("NULL argument"); return MC_EINVAL; }
+  info->n_rows = sys->n_rows;
+  info->n_cols = sys->n_cols;
+  info->nnz = sys->nnz;
+  info->n_events = sys->n_events;
+  info->first_history = sys->first;
+  info->n_histories = sys->count;
+  for (int f = 0; f < 4; ++f) info->fates[f] = sys->fates[f];
+  info->max_count = sys->max_count;
+  info->value_type = sys->value_type;
+  info->build_ms_transport = sys->ms_transport;
+  info->build_ms_assembly = sys->ms_assembly;
+  return MC_OK;
+}
+
+static int copy_ptr_u32_to_i64(const DevBuf &src, int64_t n, int64_t *dst, cudaStream_t s) {
+  std::vector<uint32_t> tmp((size_t)n);
+  MCS_CUDA(cudaMemcpyAsync(tmp.data(), src.p, n * 4, cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; ++i) dst[i] = tmp[i];
+  return MC_OK;
+}
+
+int mc_system_export_csc(const mc_system *sys, int64_t *col_ptr_host, int32_t *row_idx_host, uint32_t *counts_host,
+                         uint32_t *n_v_host, void *stream) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  cudaStream_t s = API_STREAM(stream);
+  if (col_ptr_host) MCS_TRY(copy_ptr_u32_to_i64(sys->col_ptr, sys->n_cols + 1, col_ptr_host, s));
+  if (row_idx_host && sys->nnz) MCS_CUDA(cudaMemcpyAsync(row_idx_host, sys->row_idx.p, sys->nnz * 4, cudaMemcpyDeviceToHost, s));
+  if (counts_host && sys->nnz) MCS_CUDA(cudaMemcpyAsync(counts_host, sys->csc_cnt.p, sys->nnz * 4, cudaMemcpyDeviceToHost, s));
+  if (n_v_host) MCS_CUDA(cudaMemcpyAsync(n_v_host, sys->n_v.p, sys->n_cols * 4, cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+int mc_system_export_csr(const mc_system *sys, int64_t *row_ptr_host, int32_t *col_idx_host, uint32_t *counts_host,
+                         void *stream) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  cudaStream_t s = API_STREAM(stream);
+  if (row_ptr_host) MCS_TRY(copy_ptr_u32_to_i64(sys->row_ptr, sys->n_rows + 1, row_ptr_host, s));
+  if (col_idx_host && sys->nnz) MCS_CUDA(cudaMemcpyAsync(col_idx_host, sys->col_idx.p, sys->nnz * 4, cudaMemcpyDeviceToHost, s));
+  if (counts_host && sys->nnz) MCS_CUDA(cudaMemcpyAsync(counts_host, sys->csr_cnt.p, sys->nnz * 4, cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t allow_rounding) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  if (value_type != MC_VAL_F32 && value_type != MC_VAL_F16 && value_type != MC_VAL_BF16) {
+    set_error("unknown value type %d", value_type);
+    return MC_EINVAL;
+  }
+  const uint32_t exact = value_type == MC_VAL_F32 ? (1u << 24) : value_type == MC_VAL_F16 ? 2048u : 256u;
+  if (!allow_rounding && sys->max_count > exact) {
+    set_error("largest count %u is not exact in the requested type (limit %u)", sys->max_count, exact);
+    return MC_EINVAL;
+  }
+  const int old = sys->value_type;
+  sys->value_type = value_type;
+  cudaStream_t s = nullptr;
+  int rc = make_values(sys, s);
+  if (rc == MC_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = MC_ECUDA;
+  if (rc != MC_OK) {
+    sys->value_type = old;
+    make_values(sys, s);
+    cudaStreamSynchronize(s);
+  }
+  return rc;
+}
+
+int mc_project(const mc_system *sys, const float *x_dev, float *q_dev, void *stream) {
+  clear_error();
+  if (!sys || !x_dev || !q_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return project(sys, x_dev, q_dev, API_STREAM(stream));
+}
+
+int mc_backproject(const mc_system *sys, const float *r_dev, float *b_dev, void *stream) {
+  clear_error();
+  if (!sys || !r_dev || !b_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return backproject(sys, r_dev, b_dev, API_STREAM(stream));
+}
+
+int mc_sensitivity(const mc_system *sys, double *s_dev, void *stream) {
+  clear_error();
+  if (!sys || !s_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return sensitivity(sys, s_dev, API_STREAM(stream));
+}
+
+int mc_mlem_init(mc_system *sys, const float *y_dev, float *x_dev, void *stream) {
+  clear_error();
+  if (!sys || !y_dev || !x_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return mlem_init(sys, y_dev, x_dev, API_STREAM(stream));
+}
+
+int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter, double *loglik_host,
+                 void *stream) {
+  clear_error();
+  if (!sys || !y_dev || !x_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  if (n_iter < 0) { set_error("n_iter must be >= 0"); return MC_EINVAL; }
+  cudaStream_t s = API_STREAM(stream);
+  const bool want = loglik_host != nullptr && n_iter > 0;
+  if (want && sys->ll_cap < n_iter) {
+    MCS_TRY(sys->ll.alloc((size_t)n_iter * sizeof(double), s));
+    sys->ll_cap = n_iter;
+  }
+  MCS_TRY(mlem_run(sys, y_dev, x_dev, n_iter, want, s));
+  if (want) {
+    MCS_CUDA(cudaMemcpyAsync(loglik_host, sys->ll.p, (size_t)n_iter * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaStreamSynchronize(s));
+  }
+  return MC_OK;
+}
+
+int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,
+                       uint64_t count, mc_history_record *out_host) {
+  clear_error();
+  MCS_TRY(check_phantom(phantom));
+  MCS_TRY(check_geometry(geometry, phantom));
+  if (count > 0 && !out_host) { set_error("out_host is NULL"); return MC_EINVAL; }
+  if (count == 0) return MC_OK;
+  cudaStream_t s = nullptr;
+  mc_plan pl;
+  MCS_TRY(prepare_plan(phantom, geometry, s, pl));
+  TransportSetup ts = pl.ts;
+  ts.first = first;
+  ts.count = count;
+  ts.key0 = (uint32_t)seed;
+  ts.key1 = (uint32_t)(seed >> 32);
+  DevBuf rec, ctr;
+  MCS_TRY(rec.alloc(count * sizeof(mc_history_record), s));
+  MCS_TRY(ctr.alloc(5 * sizeof(unsigned long long), s));
+  MCS_CUDA(cudaMemsetAsync(ctr.p, 0, 5 * sizeof(unsigned long long), s));
+  ts.events = nullptr;
+  ts.capacity = 0;
+  ts.cursor = ctr.as<unsigned long long>();
+  ts.fates = ctr.as<unsigned long long>() + 1;
+  ts.records = rec.as<mc_history_record>();
+  MCS_TRY(run_transport(ts, s));
+  MCS_CUDA(cudaMemcpyAsync(out_host, rec.p, count * sizeof(mc_history_record), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+int mc_debug_kn(double e_kev, int32_t precision, uint64_t seed, uint64_t n, double *cos_out_host,
+                double *eps_out_host) {
+  clear_error();
+  if (n > 0 && (!cos_out_host || !eps_out_host)) { set_error("NULL output"); return MC_EINVAL; }
+  if (!(e_kev > 0) || (precision != MC_FP32 && precision != MC_FP64)) { set_error("bad energy or precision"); return MC_EINVAL; }
+  if (n == 0) return MC_OK;
+  cudaStream_t s = nullptr;
+  DevBuf c, e;
+  MCS_TRY(c.alloc(n * sizeof(double), s));
+  MCS_TRY(e.alloc(n * sizeof(double), s));
+  if (precision == MC_FP64) MCS_TRY(launch_debug_kn_f64(e_kev, seed, n, c.as<double>(), e.as<double>(), s));
+  else MCS_TRY(launch_debug_kn_f32(e_kev, seed, n, c.as<double>(), e.as<double>(), s));
+  MCS_CUDA(cudaMemcpyAsync(cos_out_host, c.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaMemcpyAsync(eps_out_host, e.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+int mc_debug_beam(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t n,
+                  const double *p0_host, const double *d_host, double e_kev, uint64_t *through_host) {
+  clear_error();
+  MCS_TRY(check_phantom(phantom));
+  MCS_TRY(check_geometry(geometry, phantom));
+  if (!p0_host || !d_host || !through_host) { set_error("NULL argument"); return MC_EINVAL; }
+  cudaStream_t s = nullptr;
+  mc_plan pl;
+  MCS_TRY(prepare_plan(phantom, geometry, s, pl));
+  TransportSetup ts = pl.ts;
+  ts.first = 0;
+  ts.count = n;
+  ts.key0 = (uint32_t)seed;
+  ts.key1 = (uint32_t)(seed >> 32);
+  DevBuf t;
+  MCS_TRY(t.alloc(sizeof(unsigned long long), s));
+  MCS_CUDA(cudaMemsetAsync(t.p, 0, sizeof(unsigned long long), s));
+  if (geometry->precision == MC_FP64)
+    MCS_TRY(launch_debug_beam_f64(ts, n, p0_host, d_host, e_kev, t.as<unsigned long long>(), s));
+  else
+    MCS_TRY(launch_debug_beam_f32(ts, n, p0_host, d_host, e_kev, t.as<unsigned long long>(), s));
+  unsigned long long h = 0;
+  MCS_CUDA(cudaMemcpyAsync(&h, t.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  *through_host = h;
+  return MC_OK;
+}
+
+}  // extern "C"

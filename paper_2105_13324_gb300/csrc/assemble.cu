@@ -1,0 +1,444 @@
+// assemble.cu -- tally assembly: detection events (v, j) -> the count matrix
+// C_jv of Eq. (IMC) (Sec. 5.1: T_ij estimated by Monte Carlo; Sec. 2: tallies
+// are counts of histories).
+//
+// Events arrive as 64-bit keys v*M + j in arbitrary order (the transport
+// kernel appends them with atomics).  A stable LSD radix sort orders them by
+// (v, j); a run-length pass turns runs of equal keys into (v, j, count)
+// triples, which are the CSC form.  The CSR form comes from a second radix
+// sort of the (j*N + v, count) pairs.  Everything is integer work, so the
+// matrix is bit-identical from run to run.  No floating-point atomics.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mcs {
+
+// ---------------------------------------------------------------------------
+// exclusive scan (u32), reduce-then-scan over tiles of 2048 elements
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) s_warp[lane] = w;  // inclusive per warp
+  }
+  __syncthreads();
+  total = s_warp[(blockDim.x >> 5) - 1];
+  const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0u;
+  return before + x - v;
+}
+
+__global__ void scan_reduce_kernel(const uint32_t *in, uint32_t *sums, int64_t n) {
+  __shared__ uint32_t s_warp[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) acc += in[i];
+  }
+  uint32_t total;
+  block_exclusive_scan(acc, s_warp, total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_apply_kernel(const uint32_t *in, uint32_t *out, const uint32_t *offsets, int64_t n) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_items[kScanTile];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  // coalesced load into shared memory, then each thread scans 8 consecutive items
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    s_items[k * kScanThreads + threadIdx.x] = i < n ? in[i] : 0u;
+  }
+  __syncthreads();
+  uint32_t local[kScanItems];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    local[k] = acc;
+    acc += s_items[threadIdx.x * kScanItems + k];
+  }
+  uint32_t total;
+  const uint32_t pre = block_exclusive_scan(acc, s_warp, total) + (offsets ? offsets[blockIdx.x] : 0u);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s_items[threadIdx.x * kScanItems + k] = pre + local[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+    if (i < n) out[i] = s_items[k * kScanThreads + threadIdx.x];
+  }
+}
+
+int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return MC_OK;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {
+    count_launch(); scan_apply_kernel<<<1, kScanThreads, 0, s>>>(in, out, nullptr, n);
+    MCS_LAUNCHED();
+    return MC_OK;
+  }
+  DevBuf sums, offs;
+  MCS_TRY(sums.alloc(tiles * sizeof(uint32_t), s));
+  MCS_TRY(offs.alloc(tiles * sizeof(uint32_t), s));
+  count_launch(); scan_reduce_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, sums.as<uint32_t>(), n);
+  MCS_LAUNCHED();
+  MCS_TRY(exclusive_scan_u32(sums.as<uint32_t>(), offs.as<uint32_t>(), tiles, s));
+  count_launch(); scan_apply_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, offs.as<uint32_t>(), n);
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of u64 keys (optional u32 payload), 8-bit digits
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys
+
+__global__ void radix_hist_kernel(const uint64_t *keys, int64_t n, int shift, uint32_t *counts, int64_t n_tiles) {
+  __shared__ uint32_t s_hist[256];
+  s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&s_hist[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = s_hist[threadIdx.x];
+}
+
+// Stable scatter: key at tile position p goes to
+//   offset[digit][tile] + (number of earlier keys of this tile with the same digit).
+__global__ void radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
+                                     int64_t n, int shift, const uint32_t *offsets, int64_t n_tiles) {
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_wc[kSortThreads / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  s_base[threadIdx.x] = offsets[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) s_wc[w][threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    const uint64_t key = valid ? kin[i] : 0ull;
+    const uint32_t val = (valid && vin) ? vin[i] : 0u;
+    const uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) s_wc[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_base[digit] + rank;
+      for (int w = 0; w < warp; ++w) pos += s_wc[w][digit];
+      kout[pos] = key;
+      if (vout) vout[pos] = val;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      add += s_wc[w][threadIdx.x];
+      s_wc[w][threadIdx.x] = 0u;
+    }
+    s_base[threadIdx.x] += add;
+    __syncthreads();
+  }
+}
+
+int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bits,
+                   bool *result_in_alt, cudaStream_t s) {
+  *result_in_alt = false;
+  if (n <= 1 || bits <= 0) return MC_OK;
+  if (n >= (int64_t)0xFFFFFFFFll) {
+    set_error("radix sort: %lld keys exceed the 32-bit offset range", (long long)n);
+    return MC_EINVAL;
+  }
+  const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+  DevBuf counts, offsets;
+  MCS_TRY(counts.alloc(256 * n_tiles * sizeof(uint32_t), s));
+  MCS_TRY(offsets.alloc(256 * n_tiles * sizeof(uint32_t), s));
+  uint64_t *kin = keys, *kout = keys_alt;
+  uint32_t *vin = vals, *vout = vals_alt;
+  bool in_alt = false;
+  for (int shift = 0; shift < bits; shift += 8) {
+    count_launch(); radix_hist_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, n, shift, counts.as<uint32_t>(), n_tiles);
+    MCS_LAUNCHED();
+    MCS_TRY(exclusive_scan_u32(counts.as<uint32_t>(), offsets.as<uint32_t>(), 256 * n_tiles, s));
+    count_launch(); radix_scatter_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                                     offsets.as<uint32_t>(), n_tiles);
+    MCS_LAUNCHED();
+    uint64_t *tk = kin; kin = kout; kout = tk;
+    uint32_t *tv = vin; vin = vout; vout = tv;
+    in_alt = !in_alt;
+  }
+  *result_in_alt = in_alt;
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// run-length encoding of sorted keys
+// ---------------------------------------------------------------------------
+__global__ void head_flags_kernel(const uint64_t *keys, int64_t n, uint32_t *flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void compact_heads_kernel(const uint64_t *keys, const uint32_t *flags, const uint32_t *idx, int64_t n,
+                                     uint64_t *ukeys, uint32_t *upos) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (flags[i]) {
+      ukeys[idx[i]] = keys[i];
+      upos[idx[i]] = (uint32_t)i;
+    }
+  }
+}
+
+__global__ void run_lengths_kernel(const uint32_t *upos, int64_t nu, int64_t n, uint32_t *cnt) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x)
+    cnt[u] = (u + 1 < nu ? upos[u + 1] : (uint32_t)n) - upos[u];
+}
+
+// (v*M + j) -> row j, column v; histogram of the column (or row) index.
+__global__ void split_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, uint32_t *major_out,
+                                  uint32_t *minor_out, uint32_t *major_hist) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ukeys[u];
+    const uint32_t major = (uint32_t)(k / m), minor = (uint32_t)(k % m);
+    if (major_out) major_out[u] = major;
+    minor_out[u] = minor;
+    atomicAdd(&major_hist[major], 1u);
+  }
+}
+
+__global__ void transpose_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, uint64_t n_cols,
+                                      uint64_t *tkeys) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ukeys[u];
+    tkeys[u] = (k % m) * n_cols + (k / m);
+  }
+}
+
+// n_v = #{h in [first, first+count) : h mod N = v}
+__global__ void histories_per_voxel_kernel(uint64_t first, uint64_t count, uint64_t n_vox, uint32_t *n_v,
+                                           float *inv_n) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_vox; v += (uint64_t)gridDim.x * blockDim.x) {
+    // number of h in [0, x) with h = v (mod N)
+    auto below = [&](uint64_t x) -> uint64_t { return x > v ? (x - v - 1) / n_vox + 1 : 0; };
+    const uint64_t c = below(first + count) - below(first);
+    n_v[v] = (uint32_t)c;
+    inv_n[v] = c ? (float)(1.0 / (double)c) : 0.0f;
+  }
+}
+
+// S_v = sum_j C_jv over CSC column v, and the largest count.
+__global__ void column_sums_kernel(const uint32_t *col_ptr, const uint32_t *cnt, int64_t n_cols, double *colsum,
+                                   float *inv_colsum, unsigned int *max_count) {
+  uint32_t mymax = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_cols; v += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t acc = 0;
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) {
+      acc += cnt[k];
+      mymax = cnt[k] > mymax ? cnt[k] : mymax;
+    }
+    colsum[v] = (double)acc;
+    inv_colsum[v] = acc ? (float)(1.0 / (double)acc) : 0.0f;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, mymax, o);
+    mymax = y > mymax ? y : mymax;
+  }
+  if ((threadIdx.x & 31) == 0 && mymax) atomicMax(max_count, mymax);
+}
+
+static int grid_for(int64_t n, int threads = 256) {
+  int64_t g = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)device_sm_count() * 32;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+static int bits_for(uint64_t range) {
+  int b = 0;
+  while (b < 64 && (range >> b) != 0) ++b;
+  return b;
+}
+
+int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
+  const uint64_t M = (uint64_t)sys->n_rows, N = (uint64_t)sys->n_cols;
+  // n_v and 1/n_v
+  MCS_TRY(sys->n_v.alloc(N * sizeof(uint32_t), s));
+  MCS_TRY(sys->inv_n.alloc(N * sizeof(float), s));
+  count_launch(); histories_per_voxel_kernel<<<grid_for((int64_t)N), 256, 0, s>>>(sys->first, sys->count, N, sys->n_v.as<uint32_t>(),
+                                                                   sys->inv_n.as<float>());
+  MCS_LAUNCHED();
+
+  // 1. sort events by (v, j)
+  DevBuf alt;
+  MCS_TRY(alt.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint64_t), s));
+  bool in_alt = false;
+  MCS_TRY(radix_sort_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), nullptr, nullptr, n, bits_for(M * N - 1), &in_alt, s));
+  const uint64_t *sorted = in_alt ? alt.as<uint64_t>() : keys.as<uint64_t>();
+
+  // 2. run-length encode
+  int64_t nu = 0;
+  DevBuf ukeys, ucnt;
+  if (n > 0) {
+    DevBuf flags, idx, upos;
+    MCS_TRY(flags.alloc(n * sizeof(uint32_t), s));
+    MCS_TRY(idx.alloc(n * sizeof(uint32_t), s));
+    count_launch(); head_flags_kernel<<<grid_for(n), 256, 0, s>>>(sorted, n, flags.as<uint32_t>());
+    MCS_LAUNCHED();
+    MCS_TRY(exclusive_scan_u32(flags.as<uint32_t>(), idx.as<uint32_t>(), n, s));
+    uint32_t last_idx = 0, last_flag = 0;
+    MCS_CUDA(cudaMemcpyAsync(&last_idx, idx.as<uint32_t>() + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaMemcpyAsync(&last_flag, flags.as<uint32_t>() + (n - 1), 4, cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaStreamSynchronize(s));
+    nu = (int64_t)last_idx + last_flag;
+    MCS_TRY(ukeys.alloc(nu * sizeof(uint64_t), s));
+    MCS_TRY(upos.alloc(nu * sizeof(uint32_t), s));
+    MCS_TRY(ucnt.alloc(nu * sizeof(uint32_t), s));
+    count_launch(); compact_heads_kernel<<<grid_for(n), 256, 0, s>>>(sorted, flags.as<uint32_t>(), idx.as<uint32_t>(), n,
+                                                     ukeys.as<uint64_t>(), upos.as<uint32_t>());
+    MCS_LAUNCHED();
+    count_launch(); run_lengths_kernel<<<grid_for(nu), 256, 0, s>>>(upos.as<uint32_t>(), nu, n, ucnt.as<uint32_t>());
+    MCS_LAUNCHED();
+  }
+  alt.release();
+  keys.release();
+  sys->nnz = nu;
+
+  // 3. CSC: col_ptr from a histogram of v, rows and counts in sorted order
+  const size_t nnz_b = (size_t)(nu > 0 ? nu : 1);
+  {
+    DevBuf hist;
+    MCS_TRY(hist.alloc((N + 1) * sizeof(uint32_t), s));
+    MCS_CUDA(cudaMemsetAsync(hist.p, 0, (N + 1) * sizeof(uint32_t), s));
+    MCS_TRY(sys->col_ptr.alloc((N + 1) * sizeof(uint32_t), s));
+    MCS_TRY(sys->row_idx.alloc(nnz_b * sizeof(uint32_t), s));
+    MCS_TRY(sys->csc_cnt.alloc(nnz_b * sizeof(uint32_t), s));
+    if (nu > 0) {
+      count_launch(); split_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, nullptr, sys->row_idx.as<uint32_t>(),
+                                                     hist.as<uint32_t>());
+      MCS_LAUNCHED();
+      MCS_CUDA(cudaMemcpyAsync(sys->csc_cnt.p, ucnt.p, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), (int64_t)N + 1, s));
+  }
+
+  // 4. CSR: sort (j*N + v, count) pairs, then row_ptr from a histogram of j
+  {
+    DevBuf tkeys, tkeys_alt, tcnt_alt, hist;
+    MCS_TRY(hist.alloc((M + 1) * sizeof(uint32_t), s));
+    MCS_CUDA(cudaMemsetAsync(hist.p, 0, (M + 1) * sizeof(uint32_t), s));
+    MCS_TRY(sys->row_ptr.alloc((M + 1) * sizeof(uint32_t), s));
+    MCS_TRY(sys->col_idx.alloc(nnz_b * sizeof(uint32_t), s));
+    MCS_TRY(sys->csr_cnt.alloc(nnz_b * sizeof(uint32_t), s));
+    if (nu > 0) {
+      MCS_TRY(tkeys.alloc(nu * sizeof(uint64_t), s));
+      MCS_TRY(tkeys_alt.alloc(nu * sizeof(uint64_t), s));
+      MCS_TRY(tcnt_alt.alloc(nu * sizeof(uint32_t), s));
+      count_launch(); transpose_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, N, tkeys.as<uint64_t>());
+      MCS_LAUNCHED();
+      bool talt = false;
+      MCS_TRY(radix_sort_u64(tkeys.as<uint64_t>(), tkeys_alt.as<uint64_t>(), ucnt.as<uint32_t>(),
+                             tcnt_alt.as<uint32_t>(), nu, bits_for(M * N - 1), &talt, s));
+      const uint64_t *tk = talt ? tkeys_alt.as<uint64_t>() : tkeys.as<uint64_t>();
+      const uint32_t *tc = talt ? tcnt_alt.as<uint32_t>() : ucnt.as<uint32_t>();
+      count_launch(); split_keys_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, N, nullptr, sys->col_idx.as<uint32_t>(),
+                                                     hist.as<uint32_t>());
+      MCS_LAUNCHED();
+      MCS_CUDA(cudaMemcpyAsync(sys->csr_cnt.p, tc, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->row_ptr.as<uint32_t>(), (int64_t)M + 1, s));
+  }
+
+  // 5. column sums S_v and the largest count
+  {
+    MCS_TRY(sys->colsum.alloc(N * sizeof(double), s));
+    MCS_TRY(sys->inv_colsum.alloc(N * sizeof(float), s));
+    DevBuf mx;
+    MCS_TRY(mx.alloc(sizeof(unsigned int), s));
+    MCS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), s));
+    count_launch(); column_sums_kernel<<<grid_for((int64_t)N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
+                                                            (int64_t)N, sys->colsum.as<double>(),
+                                                            sys->inv_colsum.as<float>(), mx.as<unsigned int>());
+    MCS_LAUNCHED();
+    unsigned int mxh = 0;
+    MCS_CUDA(cudaMemcpyAsync(&mxh, mx.p, sizeof(mxh), cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaStreamSynchronize(s));
+    sys->max_count = mxh;
+  }
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// projector values: the counts in the storage type of sys->value_type
+// ---------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ V from_count(uint32_t c);
+template <> __device__ __forceinline__ float from_count<float>(uint32_t c) { return (float)c; }
+template <> __device__ __forceinline__ __half from_count<__half>(uint32_t c) { return __uint2half_rn(c); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_count<__nv_bfloat16>(uint32_t c) {
+  return __uint2bfloat16_rn(c);
+}
+
+template <typename V> __global__ void convert_counts_kernel(const uint32_t *cnt, int64_t n, V *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = from_count<V>(cnt[i]);
+}
+
+int make_values(mc_system *sys, cudaStream_t s) {
+  const int64_t nnz = sys->nnz;
+  const size_t es = sys->value_type == MC_VAL_F32 ? 4 : 2;
+  const size_t bytes = (size_t)(nnz > 0 ? nnz : 1) * es;
+  MCS_TRY(sys->csr_val.alloc(bytes, s));
+  MCS_TRY(sys->csc_val.alloc(bytes, s));
+  if (nnz == 0) return MC_OK;
+  const int g = grid_for(nnz);
+  if (sys->value_type == MC_VAL_F32) {
+    count_launch(); convert_counts_kernel<float><<<g, 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), nnz, sys->csr_val.as<float>());
+    count_launch(); convert_counts_kernel<float><<<g, 256, 0, s>>>(sys->csc_cnt.as<uint32_t>(), nnz, sys->csc_val.as<float>());
+  } else if (sys->value_type == MC_VAL_F16) {
+    count_launch(); convert_counts_kernel<__half><<<g, 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), nnz, sys->csr_val.as<__half>());
+    count_launch(); convert_counts_kernel<__half><<<g, 256, 0, s>>>(sys->csc_cnt.as<uint32_t>(), nnz, sys->csc_val.as<__half>());
+  } else {
+    count_launch(); convert_counts_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), nnz,
+                                                           sys->csr_val.as<__nv_bfloat16>());
+    count_launch(); convert_counts_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(sys->csc_cnt.as<uint32_t>(), nnz,
+                                                           sys->csc_val.as<__nv_bfloat16>());
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+}  // namespace mcs

@@ -1,0 +1,233 @@
+// internal.cuh -- declarations shared by the translation units of
+// libmcspect.so (not part of the public ABI; see include/mcspect.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/mcspect.h"
+
+namespace mcs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+void clear_error();
+// Counts kernel launches made by this library (reported by mc_kernel_launches).
+void count_launch();
+
+#define MCS_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      ::mcs::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? MC_ENOMEM : MC_ECUDA;                          \
+    }                                                                                         \
+  } while (0)
+
+#define MCS_LAUNCHED()                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess) {                                                                  \
+      ::mcs::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return MC_ECUDA;                                                                        \
+    }                                                                                         \
+  } while (0)
+
+#define MCS_TRY(expr)            \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != MC_OK) return rc_; \
+  } while (0)
+
+// Device buffer owned by host code; freed on destruction (stream-ordered).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; s = o.s; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  int alloc(size_t n, cudaStream_t stream) {
+    release();
+    s = stream;
+    bytes = n;
+    if (n == 0) return MC_OK;
+    cudaError_t e = cudaMallocAsync(&p, n, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      bytes = 0;
+      set_error("device allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+      return MC_ENOMEM;
+    }
+    return MC_OK;
+  }
+  void release() {
+    if (p && cudaFreeAsync(p, s) != cudaSuccess) {
+      (void)cudaGetLastError();  // e.g. the allocating stream is gone
+      cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// the system matrix (device resident)
+// ---------------------------------------------------------------------------
+}  // namespace mcs
+
+struct mc_system {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0, n_events = 0;
+  uint64_t first = 0, count = 0;
+  uint64_t fates[4] = {0, 0, 0, 0};
+  uint32_t max_count = 0;
+  int32_t value_type = MC_VAL_F32;
+  double ms_transport = 0.0, ms_assembly = 0.0;
+  // CSR (rows -> cols) and CSC (cols -> rows) of the counts C_jv
+  mcs::DevBuf row_ptr, col_idx, csr_cnt;  // u32 [M+1], u32 [nnz], u32 [nnz]
+  mcs::DevBuf col_ptr, row_idx, csc_cnt;  // u32 [N+1], u32 [nnz], u32 [nnz]
+  // projector values (counts as float / half / bfloat16)
+  mcs::DevBuf csr_val, csc_val;
+  mcs::DevBuf n_v;      // u32 [N]: histories started in voxel v
+  mcs::DevBuf inv_n;    // f32 [N]: 1/n_v (0 if n_v = 0)
+  mcs::DevBuf colsum;   // f64 [N]: S_v = sum_j C_jv
+  mcs::DevBuf inv_colsum;  // f32 [N]: 1/S_v (0 if S_v = 0)
+  // work vectors of the projectors / ML-EM
+  mcs::DevBuf xs;       // f32 [N]: x_v / n_v
+  mcs::DevBuf r;        // f32 [M]
+  mcs::DevBuf partials; // f64 [max blocks]
+  mcs::DevBuf ll;       // f64 [ll_cap]
+  int64_t ll_cap = 0;
+  int spmv_group_fwd = 4, spmv_group_bwd = 4;  // lanes per row / per column
+};
+
+namespace mcs {
+
+// ---------------------------------------------------------------------------
+// build pieces implemented in the .cu files
+// ---------------------------------------------------------------------------
+
+// Host-side description of one transport launch (built in api.cu).
+struct TransportSetup {
+  // grid
+  int nx, ny, nz;
+  double h;
+  const uint8_t *material_dev;
+  int n_mat;
+  double rho[256], zoa[256], zeff[256];
+  // camera
+  int n_views, bins_u, bins_v;
+  double start_deg, arc_deg, bin_mm, radius_mm, hole_len, hole_diam, fwhm, e0, window, photo_k;
+  const double *view_cs_dev;  // [2*V]: cos, sin of theta_k (double)
+  const float *view_cs_f_dev; // [2*V] same, float
+  const double *coef_d_dev;   // [3*n_mat] 0.1 rho, N_A Z/A, k Z^4 (double)
+  const float *coef_f_dev;    // [3*n_mat] 0.1 rho N_A Z/A, 0.1 rho k Z^4, 0 (float)
+  // run
+  uint64_t first, count;
+  uint32_t key0, key1;
+  // outputs
+  unsigned long long *events;  // key = v*M + j
+  unsigned long long capacity;
+  unsigned long long *cursor;
+  unsigned long long *fates;   // [4]
+  mc_history_record *records;  // trace mode (else null)
+  int precision;
+};
+
+int launch_transport(const TransportSetup &ts, cudaStream_t s);
+int launch_debug_kn(double e_kev, int precision, uint64_t seed, uint64_t n, double *cos_dev, double *eps_dev,
+                    cudaStream_t s);
+int launch_debug_beam(const TransportSetup &ts, uint64_t n, const double p0[3], const double d[3], double e_kev,
+                      unsigned long long *through_dev, cudaStream_t s);
+
+// Assembly: sorted events -> CSR + CSC + n_v + column sums.  `keys` holds
+// n keys (v*M + j) and is overwritten.
+int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s);
+
+// Projector value arrays for sys->value_type.
+int make_values(mc_system *sys, cudaStream_t s);
+
+// Scans / sorts (assemble.cu)
+int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bits,
+                   bool *result_in_alt, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of
+//   (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0))
+// with the key bumped by the Weyl increments after each round.
+__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                              uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// One history's stream: block b of history h is counter (b, 0, h_lo, h_hi)
+// under key (seed_lo, seed_hi); words are consumed w0, w1, w2, w3, then the
+// next block.
+struct Stream {
+  uint32_t k0, k1, h_lo, h_hi;
+  uint32_t block;
+  uint32_t w0, w1, w2, w3;
+  uint32_t left;
+  uint32_t n_draws;
+  __device__ __forceinline__ void init(uint32_t key0, uint32_t key1, uint64_t h) {
+    k0 = key0; k1 = key1;
+    h_lo = (uint32_t)h; h_hi = (uint32_t)(h >> 32);
+    block = 0; left = 0; n_draws = 0;
+  }
+  __device__ __forceinline__ uint32_t word() {
+    if (left == 0) {
+      uint32_t c0 = block, c1 = 0u, c2 = h_lo, c3 = h_hi;
+      philox4x32_10(c0, c1, c2, c3, k0, k1);
+      w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+      block += 1;
+      left = 4;
+    }
+    const uint32_t w = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    left -= 1;
+    n_draws += 1;
+    return w;
+  }
+};
+
+// Uniform in (0,1).  double: (w + 1/2) 2^-32 (exact).  float: the top 23
+// bits, (floor(w / 2^9) + 1/2) 2^-23, computed as ((w >> 8) | 1) 2^-24
+// (an odd 24-bit integer, exact in float).
+template <typename T> __device__ __forceinline__ T uniform(uint32_t w);
+template <> __device__ __forceinline__ double uniform<double>(uint32_t w) {
+  return ((double)w + 0.5) * (1.0 / 4294967296.0);
+}
+template <> __device__ __forceinline__ float uniform<float>(uint32_t w) {
+  return (float)((w >> 8) | 1u) * (1.0f / 16777216.0f);
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+int device_sm_count();
+
+}  // namespace mcs

@@ -1,0 +1,366 @@
+"""Thin ctypes binding of libmcspect.so (include/mcspect.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Device
+buffers are torch CUDA tensors (PyTorch provides device memory and streams);
+host buffers are NumPy arrays.  Function names follow the C entry points.
+
+The library is loaded from paper_2105_13324_gb300/_build/libmcspect.so; if
+it is missing, every call raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import phantoms as _ph
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
+
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EFORMAT = 0, -1, -2, -3, -4, -5
+MC_FP32, MC_FP64 = 0, 1
+MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
+FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
+
+# every symbol include/mcspect.h declares
+EXPORTED = (
+    "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
+    "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
+    "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate",
+    "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
+)
+
+RECORD_DTYPE = np.dtype([
+    ("fate", np.uint8), ("n_events", np.uint8), ("pad", np.uint16),
+    ("n_virtual", np.uint32), ("n_real", np.uint32), ("n_compton", np.uint32),
+    ("n_draws", np.uint32), ("pad2", np.uint32), ("e_final_kev", np.float64),
+    ("event_row", np.int32, (4,)),
+])
+
+
+class McError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mcspect error {code}: {msg}")
+        self.code = code
+
+
+class MCPhantom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("voxel_mm", ctypes.c_double), ("material_host", ctypes.c_void_p),
+                ("n_materials", ctypes.c_int32), ("rho_host", ctypes.c_void_p),
+                ("z_over_a_host", ctypes.c_void_p), ("z_eff_host", ctypes.c_void_p)]
+
+
+class MCGeometry(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int32), ("start_deg", ctypes.c_double), ("arc_deg", ctypes.c_double),
+                ("n_bins_u", ctypes.c_int32), ("n_bins_v", ctypes.c_int32), ("bin_mm", ctypes.c_double),
+                ("radius_mm", ctypes.c_double), ("hole_len_mm", ctypes.c_double),
+                ("hole_diam_mm", ctypes.c_double), ("fwhm_mm", ctypes.c_double), ("e0_kev", ctypes.c_double),
+                ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double), ("precision", ctypes.c_int32)]
+
+
+class MCSystemInfo(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_events", ctypes.c_int64), ("first_history", ctypes.c_uint64),
+                ("n_histories", ctypes.c_uint64), ("fates", ctypes.c_uint64 * 4), ("max_count", ctypes.c_uint32),
+                ("value_type", ctypes.c_int32), ("build_ms_transport", ctypes.c_double),
+                ("build_ms_assembly", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libmcspect.so (build it first with paper_2105_13324_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libmcspect.so not found at {p}: run paper_2105_13324_gb300.build.build()")
+        L = ctypes.CDLL(p)
+        vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "mc_plan_create": [vp, vp, vp, vp],
+            "mc_plan_build": [vp, u64, u64, u64, vp, vp],
+            "mc_plan_free": [vp],
+            "mc_build_system": [vp, vp, u64, u64, vp, vp],
+            "mc_build_system_range": [vp, vp, u64, u64, u64, vp, vp],
+            "mc_system_from_events": [i64, i64, vp, vp, i64, u64, u64, vp, vp],
+            "mc_system_free": [vp],
+            "mc_system_info_get": [vp, vp],
+            "mc_system_export_csc": [vp, vp, vp, vp, vp, vp],
+            "mc_system_export_csr": [vp, vp, vp, vp, vp],
+            "mc_system_set_value_type": [vp, i32, i32],
+            "mc_project": [vp, vp, vp, vp],
+            "mc_backproject": [vp, vp, vp, vp],
+            "mc_sensitivity": [vp, vp, vp],
+            "mc_mlem_init": [vp, vp, vp, vp],
+            "mlem_iterate": [vp, vp, vp, i32, vp, vp],
+            "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
+            "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
+            "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.mc_kernel_launches.argtypes = []
+        L.mc_kernel_launches.restype = ctypes.c_uint64
+        L.mc_last_error.argtypes = []
+        L.mc_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != MC_OK:
+        raise McError(rc, load().mc_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _Inputs:
+    """C structs for a Phantom + Geometry, keeping NumPy buffers alive."""
+
+    def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int):
+        self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
+        self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
+        self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
+        self.zeff = np.ascontiguousarray(phantom.z_eff, dtype=np.float64)
+        nz, ny, nx = self.material.shape
+        self.ph = MCPhantom(nx, ny, nz, float(phantom.voxel_mm), self.material.ctypes.data, len(self.rho),
+                            self.rho.ctypes.data, self.zoa.ctypes.data, self.zeff.ctypes.data)
+        g = geometry
+        self.geo = MCGeometry(g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
+                              float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
+                              float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
+                              int(precision))
+
+
+def _precision(p):
+    if p in ("fp32", MC_FP32):
+        return MC_FP32
+    if p in ("fp64", MC_FP64):
+        return MC_FP64
+    raise ValueError(f"precision must be 'fp32' or 'fp64', got {p!r}")
+
+
+class System:
+    """Owner of an mc_system handle (device-resident system matrix)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("system was freed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = MCSystemInfo()
+        _check(load().mc_system_info_get(self.handle, ctypes.byref(inf)))
+        return {"n_rows": inf.n_rows, "n_cols": inf.n_cols, "nnz": inf.nnz, "n_events": inf.n_events,
+                "first_history": inf.first_history, "n_histories": inf.n_histories,
+                "fates": [int(v) for v in inf.fates], "max_count": inf.max_count,
+                "value_type": inf.value_type, "build_ms_transport": inf.build_ms_transport,
+                "build_ms_assembly": inf.build_ms_assembly}
+
+    @property
+    def shape(self):
+        i = self.info()
+        return i["n_rows"], i["n_cols"]
+
+    def export_csc(self, stream=None):
+        i = self.info()
+        cp = np.zeros(i["n_cols"] + 1, np.int64)
+        ri = np.zeros(max(i["nnz"], 1), np.int32)
+        cnt = np.zeros(max(i["nnz"], 1), np.uint32)
+        nv = np.zeros(i["n_cols"], np.uint32)
+        _check(load().mc_system_export_csc(self.handle, cp.ctypes.data, ri.ctypes.data, cnt.ctypes.data,
+                                           nv.ctypes.data, _stream_ptr(stream)))
+        return cp, ri[:i["nnz"]], cnt[:i["nnz"]], nv
+
+    def export_csr(self, stream=None):
+        i = self.info()
+        rp = np.zeros(i["n_rows"] + 1, np.int64)
+        ci = np.zeros(max(i["nnz"], 1), np.int32)
+        cnt = np.zeros(max(i["nnz"], 1), np.uint32)
+        _check(load().mc_system_export_csr(self.handle, rp.ctypes.data, ci.ctypes.data, cnt.ctypes.data,
+                                           _stream_ptr(stream)))
+        return rp, ci[:i["nnz"]], cnt[:i["nnz"]]
+
+    def set_value_type(self, value_type, allow_rounding=False):
+        vt = {"f32": MC_VAL_F32, "f16": MC_VAL_F16, "bf16": MC_VAL_BF16}.get(value_type, value_type)
+        _check(load().mc_system_set_value_type(self.handle, int(vt), int(bool(allow_rounding))))
+
+    def free(self):
+        if self._h:
+            _check(load().mc_system_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.mc_system_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owner of an mc_plan handle: phantom + geometry resident on the device."""
+
+    def __init__(self, phantom, geometry, precision="fp32", stream=None):
+        inp = _Inputs(phantom, geometry, _precision(precision))
+        h = ctypes.c_void_p()
+        _check(load().mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), _stream_ptr(stream),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    def build(self, first: int, count: int, seed: int, stream=None) -> System:
+        return mc_plan_build(self, first, count, seed, stream)
+
+    def free(self):
+        if self._h:
+            _check(load().mc_plan_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.mc_plan_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def mc_plan_create(phantom, geometry, precision="fp32", stream=None) -> Plan:
+    return Plan(phantom, geometry, precision, stream)
+
+
+def mc_plan_build(plan: Plan, first: int, count: int, seed: int, stream=None) -> System:
+    if not plan._h:
+        raise ValueError("plan was freed")
+    h = ctypes.c_void_p()
+    _check(load().mc_plan_build(plan._h, int(first), int(count), int(seed), _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_plan_free(plan: Plan):
+    plan.free()
+
+
+def mc_kernel_launches() -> int:
+    return int(load().mc_kernel_launches())
+
+
+def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="fp32", stream=None) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision))
+    h = ctypes.c_void_p()
+    _check(load().mc_build_system(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(n_histories), int(seed),
+                                  _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_build_system_range(phantom, geometry, first: int, count: int, seed: int, precision="fp32",
+                          stream=None) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision))
+    h = ctypes.c_void_p()
+    _check(load().mc_build_system_range(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(first), int(count),
+                                        int(seed), _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_system_from_events(n_rows: int, n_cols: int, rows, cols, first: int, count: int, stream=None) -> System:
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    if r.shape != c.shape:
+        raise ValueError("rows and cols differ in length")
+    h = ctypes.c_void_p()
+    _check(load().mc_system_from_events(int(n_rows), int(n_cols), r.ctypes.data, c.ctypes.data, int(r.size),
+                                        int(first), int(count), _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_project(sys: System, x, q, stream=None):
+    import torch
+    _check(load().mc_project(sys.handle, _dev_ptr(x, torch.float32), _dev_ptr(q, torch.float32),
+                             _stream_ptr(stream)))
+    return q
+
+
+def mc_backproject(sys: System, r, b, stream=None):
+    import torch
+    _check(load().mc_backproject(sys.handle, _dev_ptr(r, torch.float32), _dev_ptr(b, torch.float32),
+                                 _stream_ptr(stream)))
+    return b
+
+
+def mc_sensitivity(sys: System, s, stream=None):
+    import torch
+    _check(load().mc_sensitivity(sys.handle, _dev_ptr(s, torch.float64), _stream_ptr(stream)))
+    return s
+
+
+def mc_mlem_init(sys: System, y, x, stream=None):
+    import torch
+    _check(load().mc_mlem_init(sys.handle, _dev_ptr(y, torch.float32), _dev_ptr(x, torch.float32),
+                               _stream_ptr(stream)))
+    return x
+
+
+def mlem_iterate(sys: System, y, x, n_iter: int, loglik: bool = False, stream=None):
+    """n_iter ML-EM updates of x in place; returns the log-likelihoods of the
+    iterates before each update when loglik is set (else None)."""
+    import torch
+    ll = np.zeros(max(n_iter, 1), np.float64) if loglik else None
+    _check(load().mlem_iterate(sys.handle, _dev_ptr(y, torch.float32), _dev_ptr(x, torch.float32), int(n_iter),
+                               ll.ctypes.data if loglik else None, _stream_ptr(stream)))
+    return ll[:n_iter] if loglik else None
+
+
+def mc_trace_histories(phantom, geometry, seed: int, first: int, count: int, precision="fp64") -> np.ndarray:
+    inp = _Inputs(phantom, geometry, _precision(precision))
+    out = np.zeros(count, RECORD_DTYPE)
+    _check(load().mc_trace_histories(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(seed), int(first),
+                                     int(count), out.ctypes.data))
+    return out
+
+
+def mc_debug_kn(e_kev: float, seed: int, n: int, precision="fp64"):
+    c = np.zeros(n, np.float64)
+    e = np.zeros(n, np.float64)
+    _check(load().mc_debug_kn(float(e_kev), _precision(precision), int(seed), int(n), c.ctypes.data, e.ctypes.data))
+    return c, e
+
+
+def mc_debug_beam(phantom, geometry, seed: int, n: int, p0, d, e_kev: float, precision="fp64") -> int:
+    inp = _Inputs(phantom, geometry, _precision(precision))
+    p = np.ascontiguousarray(p0, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    out = ctypes.c_uint64(0)
+    _check(load().mc_debug_beam(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(seed), int(n), p.ctypes.data,
+                                dd.ctypes.data, float(e_kev), ctypes.byref(out)))
+    return int(out.value)

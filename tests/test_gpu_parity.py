@@ -1,0 +1,313 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Transport: per-history traces in FP64 verification mode (>= 99.99 % of
+histories identical), bit-exact count matrices from the same histories,
+FP32 tallies within 3 sigma of the FP64 oracle on the same streams.
+Assembly: bit-exact CSC/CSR from an oracle event list.  Reconstruction:
+projectors and ML-EM in FP32 against the FP64 oracle on the same matrix
+(relative L2 <= 1e-5).  Edge cases: empty and single-event matrices,
+ragged sizes, a vacuum phantom.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from paper_2105_13324_gb300 import phantoms as P
+
+pytestmark = pytest.mark.gpu
+
+MLEM_TOL = 1e-5   # relative L2, FP32 GPU vs FP64 oracle on the same matrix
+
+
+@pytest.fixture(scope="module")
+def mc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2105_13324_gb300 import build as B
+    from paper_2105_13324_gb300 import mcspect
+    mcspect.load(B.build())
+    return mcspect
+
+
+def _dev(a, dtype=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _compare_traces(g, o):
+    same = ((g["fate"] == o["fate"]) & (g["n_virtual"] == o["n_virtual"]) & (g["n_real"] == o["n_real"])
+            & (g["n_compton"] == o["n_compton"]) & (g["n_draws"] == o["n_draws"])
+            & (g["n_events"] == o["n_events"]) & np.all(g["event_row"] == o["event_row"], axis=1)
+            & (np.abs(g["e_final_kev"] - o["e_final_kev"]) <= 1e-12 * o["e_final_kev"]))
+    return same
+
+
+# ---------------------------------------------------------------------------
+# transport
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,first,count", [("water32", 0, 2_000_000), ("torso64", 7_777_777, 300_000)])
+def test_fp64_trace_matches_oracle(mc, name, first, count):
+    w = P.workload(name)
+    g = mc.mc_trace_histories(w.phantom, w.geometry, w.seed, first, count, precision="fp64")
+    o = oracle.trace(oracle.Problem(w.phantom, w.geometry), w.seed, first, count)
+    same = _compare_traces(g, o)
+    frac = same.mean()
+    bad = np.nonzero(~same)[0][:10]
+    assert frac >= 0.9999, (frac, [(int(first + i), g[i], o[i]) for i in bad])
+    assert g["n_events"].sum() > 0
+
+
+def test_fp64_matrix_is_bit_exact(mc):
+    w = P.workload("water32")
+    pr = oracle.Problem(w.phantom, w.geometry)
+    H = w.n_histories
+    sysm = mc.mc_build_system(w.phantom, w.geometry, H, w.seed, precision="fp64")
+    info = sysm.info()
+    a_orc, c_orc, nv_orc, fates = oracle.build_system(pr, w.seed, H)
+    assert info["fates"] == [int(f) for f in fates]
+    cp, ri, cnt, nv = sysm.export_csc()
+    np.testing.assert_array_equal(nv, nv_orc)
+    np.testing.assert_array_equal(cp, c_orc.indptr)
+    np.testing.assert_array_equal(ri, c_orc.indices)
+    np.testing.assert_array_equal(cnt, c_orc.data)
+    rp, ci, cnt_r = sysm.export_csr()
+    c_csr = sp.csr_matrix(c_orc)
+    c_csr.sort_indices()
+    np.testing.assert_array_equal(rp, c_csr.indptr)
+    np.testing.assert_array_equal(ci, c_csr.indices)
+    np.testing.assert_array_equal(cnt_r, c_csr.data)
+    assert info["n_events"] == int(c_orc.sum())
+
+
+def _tally_close(c_gpu, c_orc):
+    d = np.abs(c_gpu - c_orc)
+    lim = 3.0 * np.sqrt(c_gpu + c_orc) + 1e-12
+    return np.all((d <= lim) | (d == 0))
+
+
+@pytest.mark.parametrize("name,H", [("water32", 2_000_000), ("torso64", 3_000_000)])
+def test_fp32_tallies_within_3_sigma_of_oracle(mc, name, H):
+    w = P.workload(name)
+    pr = oracle.Problem(w.phantom, w.geometry)
+    sysm = mc.mc_build_system(w.phantom, w.geometry, H, w.seed, precision="fp32")
+    cp, ri, cnt, nv = sysm.export_csc()
+    c_gpu = sp.csc_matrix((cnt.astype(np.float64), ri, cp), shape=(pr.n_rows, pr.n_voxels))
+    _, c_orc, nv_orc, fates = oracle.build_system(pr, w.seed, H)
+    c_orc = c_orc.astype(np.float64)
+    np.testing.assert_array_equal(nv, nv_orc)
+    info = sysm.info()
+    assert sum(info["fates"]) == H and info["fates"][3] == 0
+    for f in range(3):   # fates: same streams, so nearly identical
+        assert abs(info["fates"][f] - int(fates[f])) <= 3 * np.sqrt(info["fates"][f] + int(fates[f])) + 1
+    assert _tally_close(np.asarray(c_gpu.sum(axis=0)).ravel(), np.asarray(c_orc.sum(axis=0)).ravel())
+    assert _tally_close(np.asarray(c_gpu.sum(axis=1)).ravel(), np.asarray(c_orc.sum(axis=1)).ravel())
+    diff = (c_gpu - c_orc).tocoo()
+    both = (c_gpu + c_orc).tocsr()
+    lim = 3.0 * np.sqrt(np.asarray(both[diff.row, diff.col]).ravel())
+    assert np.all(np.abs(diff.data) <= lim + 1e-12)
+    # shared streams: the vast majority of entries agree exactly
+    assert abs(c_gpu - c_orc).sum() <= 0.01 * c_orc.sum() + 5
+
+
+def test_fp64_compton_sampler_matches_oracle(mc):
+    c_g, e_g = mc.mc_debug_kn(140.5, 21, 200_000, precision="fp64")
+    c_o, e_o, _ = oracle.kn_sample(140.5, 21, 200_000)
+    np.testing.assert_array_equal(c_g, c_o)
+    np.testing.assert_allclose(e_g, e_o, rtol=1e-15)
+
+
+def test_fp32_compton_sampler_follows_klein_nishina(mc):
+    from scipy import stats
+    c_g, e_g = mc.mc_debug_kn(140.5, 22, 400_000, precision="fp32")
+    c_o, e_o, _ = oracle.kn_sample(140.5, 22, 400_000)
+    # same streams: the 23-bit uniforms round differently only near rejection edges
+    assert np.mean(np.abs(c_g - c_o) < 1e-6) > 0.999
+    assert stats.ks_2samp(c_g, c_o).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_beam_transmission_matches_oracle(mc, precision):
+    ph = P.slab_phantom(40, 4.0, P.WATER, 96.0, (P.BONE,))
+    g = P.spect_geometry(1, 180.0, 8, 4.0, 40, 4.0)
+    pr = oracle.Problem(ph, g)
+    p0, d = (-80.0 + 1e-9, 0.5, 0.5), (1.0, 0.0, 0.0)
+    n = 400_000
+    got = mc.mc_debug_beam(ph, g, 5, n, p0, d, 140.5, precision=precision)
+    want = oracle.beam(pr, 5, n, p0, d, 140.5)
+    if precision == "fp64":
+        assert got == want
+    else:
+        assert abs(got - want) <= 3 * np.sqrt(want) + 1
+
+
+def test_vacuum_phantom_only_collimator_acceptance(mc):
+    ph = P.vacuum_phantom(4, 1.0)
+    g = P.Geometry(n_views=8, arc_deg=360.0, n_bins_u=64, n_bins_v=64, bin_mm=4.0,
+                   radius_mm=P.front_face_radius(4, 1.0), hole_len_mm=5.0, hole_diam_mm=1.5, fwhm_mm=0.5)
+    pr = oracle.Problem(ph, g)
+    H = 500_000
+    sysm = mc.mc_build_system(ph, g, H, 9, precision="fp64")
+    _, c_orc, _, fates = oracle.build_system(pr, 9, H)
+    cp, ri, cnt, _ = sysm.export_csc()
+    np.testing.assert_array_equal(cnt, c_orc.data)
+    np.testing.assert_array_equal(ri, c_orc.indices)
+    assert sysm.info()["fates"][2] == H
+
+
+def test_history_ranges_add_up(mc):
+    w = P.workload("torso64")
+    H, m = 1_000_000, 377_777
+    full = mc.mc_build_system(w.phantom, w.geometry, H, w.seed, precision="fp32")
+    a = mc.mc_build_system_range(w.phantom, w.geometry, 0, m, w.seed, precision="fp32")
+    b = mc.mc_build_system_range(w.phantom, w.geometry, m, H - m, w.seed, precision="fp32")
+    M, N = full.shape
+
+    def mat(s):
+        cp, ri, cnt, nv = s.export_csc()
+        return sp.csc_matrix((cnt.astype(np.int64), ri, cp), shape=(M, N)), nv.astype(np.int64)
+
+    cf, nf = mat(full)
+    ca, na = mat(a)
+    cb, nb = mat(b)
+    assert (cf != ca + cb).nnz == 0
+    np.testing.assert_array_equal(nf, na + nb)
+
+
+# ---------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_rows,n_cols,n_events,seed", [
+    (37, 23, 0, 1), (37, 23, 1, 2), (1, 1, 1000, 3), (5000, 3001, 123_457, 4), (65537, 40000, 2_000_003, 5)])
+def test_assembly_from_events_is_bit_exact(mc, n_rows, n_cols, n_events, seed):
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, n_rows, n_events).astype(np.int32)
+    cols = (rng.zipf(1.3, n_events) % n_cols).astype(np.int32)
+    sysm = mc.mc_system_from_events(n_rows, n_cols, rows, cols, 0, 10 * n_cols + 3)
+    want = oracle.system_counts(rows, cols, n_rows, n_cols)
+    cp, ri, cnt, nv = sysm.export_csc()
+    np.testing.assert_array_equal(cp, want.indptr)
+    np.testing.assert_array_equal(ri, want.indices)
+    np.testing.assert_array_equal(cnt, want.data)
+    np.testing.assert_array_equal(nv, oracle.histories_per_voxel(n_cols, 0, 10 * n_cols + 3))
+    rp, ci, cr = sysm.export_csr()
+    wr = sp.csr_matrix(want)
+    wr.sort_indices()
+    np.testing.assert_array_equal(rp, wr.indptr)
+    np.testing.assert_array_equal(ci, wr.indices)
+    np.testing.assert_array_equal(cr, wr.data)
+    info = sysm.info()
+    assert info["nnz"] == want.nnz and info["n_events"] == n_events
+    assert info["max_count"] == (int(want.data.max()) if want.nnz else 0)
+
+
+# ---------------------------------------------------------------------------
+# projectors and ML-EM (oracle matrix uploaded as events)
+# ---------------------------------------------------------------------------
+def _oracle_problem(name, H, seed_shift=0):
+    w = P.workload(name)
+    pr = oracle.Problem(w.phantom, w.geometry)
+    rows, cols, _ = oracle.run(pr, w.seed + seed_shift, 0, H)
+    c = oracle.system_counts(rows, cols, pr.n_rows, pr.n_voxels)
+    nv = oracle.histories_per_voxel(pr.n_voxels, 0, H)
+    a = oracle.system_matrix(c, nv)
+    return w, pr, rows, cols, a
+
+
+@pytest.fixture(scope="module")
+def torso_small(mc):
+    w, pr, rows, cols, a = _oracle_problem("torso64", 20_000_000)
+    _, _, _, _, a_truth = _oracle_problem("torso64", 20_000_000, seed_shift=1000)
+    ybar = a_truth @ w.phantom.activity.ravel().astype(np.float64)
+    y = P.poisson_counts(ybar, w.total_counts, w.noise_seed)
+    sysm = mc.mc_system_from_events(pr.n_rows, pr.n_voxels, rows, cols.astype(np.int32), 0, 20_000_000)
+    return w, pr, a, y, sysm
+
+
+def test_projectors_match_oracle(mc, torso_small):
+    import torch
+    w, pr, a, y, sysm = torso_small
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.0, 2.0, pr.n_voxels).astype(np.float32)
+    q = torch.zeros(pr.n_rows, dtype=torch.float32, device="cuda")
+    mc.mc_project(sysm, _dev(x), q)
+    want_q = a @ x.astype(np.float64)
+    assert _rel_l2(q.cpu().numpy(), want_q) < 1e-6
+    np.testing.assert_allclose(q.cpu().numpy(), want_q, rtol=1e-5, atol=1e-6 * want_q.max())
+    r = rng.uniform(0.0, 2.0, pr.n_rows).astype(np.float32)
+    b = torch.zeros(pr.n_voxels, dtype=torch.float32, device="cuda")
+    mc.mc_backproject(sysm, _dev(r), b)
+    want_b = a.T @ r.astype(np.float64)
+    assert _rel_l2(b.cpu().numpy(), want_b) < 1e-6
+    s = torch.zeros(pr.n_voxels, dtype=torch.float64, device="cuda")
+    mc.mc_sensitivity(sysm, s)
+    np.testing.assert_allclose(s.cpu().numpy(), oracle.sensitivity(a), rtol=1e-13)
+
+
+def test_mlem_matches_oracle(mc, torso_small):
+    import torch
+    w, pr, a, y, sysm = torso_small
+    yd = _dev(y)
+    x = torch.zeros(pr.n_voxels, dtype=torch.float32, device="cuda")
+    mc.mc_mlem_init(sysm, yd, x)
+    x0 = oracle.mlem_init(a, y)
+    assert _rel_l2(x.cpu().numpy(), x0) < 1e-7
+    ll = mc.mlem_iterate(sysm, yd, x, w.mlem_iters, loglik=True)
+    xo, llo = oracle.mlem(a, y, x0, w.mlem_iters, with_loglik=True)
+    err = _rel_l2(x.cpu().numpy(), xo)
+    assert err <= MLEM_TOL, err
+    np.testing.assert_allclose(ll, llo, rtol=1e-6)
+    assert np.all(x.cpu().numpy() >= 0)
+    # continuing in two calls equals one call of the summed length
+    x2 = torch.zeros_like(x)
+    mc.mc_mlem_init(sysm, yd, x2)
+    mc.mlem_iterate(sysm, yd, x2, 20)
+    mc.mlem_iterate(sysm, yd, x2, w.mlem_iters - 20)
+    assert torch.equal(x2, x)
+
+
+def test_mlem_on_degenerate_systems(mc):
+    import torch
+    # empty matrix: every voxel has zero sensitivity -> zeros, no NaN
+    s0 = mc.mc_system_from_events(10, 7, np.zeros(0, np.int32), np.zeros(0, np.int32), 0, 70)
+    y = _dev(np.arange(10, dtype=np.float32))
+    x = torch.ones(7, dtype=torch.float32, device="cuda")
+    mc.mc_mlem_init(s0, y, x)
+    ll = mc.mlem_iterate(s0, y, x, 3, loglik=True)
+    assert torch.count_nonzero(x) == 0 and np.all(np.isfinite(ll) | (ll == -np.inf))
+    # single event: diagonal 1x1 problem converges in one step
+    s1 = mc.mc_system_from_events(3, 2, np.array([1], np.int32), np.array([0], np.int32), 0, 4)
+    y = _dev(np.array([0.0, 6.0, 0.0], np.float32))
+    x = torch.ones(2, dtype=torch.float32, device="cuda")
+    mc.mlem_iterate(s1, y, x, 1)
+    # A[1,0] = 1 / n_0 = 1/2  ->  x_0 = y_1 / A = 12
+    np.testing.assert_allclose(x.cpu().numpy(), [12.0, 0.0], rtol=1e-6)
+
+
+@pytest.mark.parametrize("vt,tol", [("f16", 1e-5), ("bf16", 1e-5)])
+def test_reduced_precision_values_exact_counts(mc, torso_small, vt, tol):
+    import torch
+    w, pr, a, y, sysm = torso_small
+    info = sysm.info()
+    limit = 2048 if vt == "f16" else 256
+    if info["max_count"] > limit:
+        pytest.skip("counts not exact in this type")
+    yd = _dev(y)
+    xs = []
+    for t in ("f32", vt):
+        sysm.set_value_type(t)
+        x = torch.zeros(pr.n_voxels, dtype=torch.float32, device="cuda")
+        mc.mc_mlem_init(sysm, yd, x)
+        mc.mlem_iterate(sysm, yd, x, 20)
+        xs.append(x.cpu().numpy())
+    sysm.set_value_type("f32")
+    assert _rel_l2(xs[1], xs[0]) < tol
