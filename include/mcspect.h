@@ -105,7 +105,9 @@ typedef struct mc_system_info {
   uint64_t fates[4];     /* ABSORBED, BELOW_WINDOW, ESCAPE, CAP */
   uint32_t max_count;    /* largest C_jv */
   int32_t value_type;    /* MC_VAL_* used by the projectors */
-  double build_ms_transport, build_ms_assembly; /* device time of the last build */
+  double build_ms_transport; /* device time of the build's transport kernel */
+  double build_ms_assembly;  /* ... of matrix assembly (sort, CSR/CSC, sums) */
+  double build_ms_detect;    /* ... of the collimator/detector kernel */
 } mc_system_info;
 
 /* Per-history trace (verification): 48 bytes, this exact layout. */

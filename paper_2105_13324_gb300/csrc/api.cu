@@ -62,7 +62,8 @@ int sensitivity(const mc_system *sys, double *out, cudaStream_t s);
 int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s);
 int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll, cudaStream_t s);
 int forward_blocks(const mc_system *sys);
-void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf);
+void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
+                          std::vector<float> &sig_tab);
 
 static constexpr double kPiHost = 3.14159265358979323846;
 
@@ -128,7 +129,7 @@ static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
 // the attenuation coefficients, ready for any number of builds.
 struct mc_plan {
   mcs::TransportSetup ts;
-  mcs::DevBuf material, views_d, views_f, coef_d, coef_f;
+  mcs::DevBuf material, views_d, views_f, coef_d, coef_f, sig_tab;
 };
 
 namespace mcs {
@@ -164,12 +165,14 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
     vf[2 * k + 1] = (float)vd[2 * k + 1];
   }
   std::vector<double> cd;
-  std::vector<float> cf;
-  compute_coefficients(ts, cd, cf);
+  std::vector<float> cf, tab;
+  compute_coefficients(ts, cd, cf, tab);
   MCS_TRY(pl.views_d.alloc(vd.size() * sizeof(double), s));
   MCS_TRY(pl.views_f.alloc(vf.size() * sizeof(float), s));
   MCS_TRY(pl.coef_d.alloc(cd.size() * sizeof(double), s));
   MCS_TRY(pl.coef_f.alloc(cf.size() * sizeof(float), s));
+  MCS_TRY(pl.sig_tab.alloc(tab.size() * sizeof(float), s));
+  MCS_CUDA(cudaMemcpyAsync(pl.sig_tab.p, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   MCS_CUDA(cudaMemcpyAsync(pl.views_d.p, vd.data(), vd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   MCS_CUDA(cudaMemcpyAsync(pl.views_f.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   MCS_CUDA(cudaMemcpyAsync(pl.coef_d.p, cd.data(), cd.size() * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -179,6 +182,7 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
   ts.view_cs_f_dev = pl.views_f.as<float>();
   ts.coef_d_dev = pl.coef_d.as<double>();
   ts.coef_f_dev = pl.coef_f.as<float>();
+  ts.sig_tab_dev = pl.sig_tab.as<float>();
   return MC_OK;
 }
 
@@ -234,20 +238,31 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   sys->count = count;
   int rc;
   // Event capacity: the unattenuated per-view acceptance (d/L)^2/16 per
-  // history, 25 % headroom; rerun with the exact size if it overflows.
-  const double acc = (ts.hole_diam / ts.hole_len) * (ts.hole_diam / ts.hole_len) / 16.0;
+  // history, 25 % headroom.  Escape-queue capacity: an isotropic photon has
+  // |d_z| below the collimator's acceptance bound with probability ~w_max.
+  // Both are rerun with the exact sizes if they overflow.
+  const double tan_max = ts.hole_diam / ts.hole_len;
+  const double acc = tan_max * tan_max / 16.0;
   double est = (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
   if (est > 4.0e9) est = 4.0e9;
-  unsigned long long cap = (unsigned long long)est;
-  DevBuf events, ctr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
-  struct EvGuard { cudaEvent_t a, b, c; ~EvGuard() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); if (c) cudaEventDestroy(c); } } eg{e0, e1, e2};
-  if ((rc = ctr.alloc(5 * sizeof(unsigned long long), s))) return fail(rc);
-  unsigned long long hctr[5];
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  const double w_max = tan_max / std::sqrt(1.0 + tan_max * tan_max) * 1.02 + 1e-6;
+  double est_q = (double)count * w_max * 1.1 + 65536.0;
+  if (est_q > (double)count) est_q = (double)count;
+  unsigned long long cap = (unsigned long long)est, cap_q = (unsigned long long)est_q;
+  DevBuf events, ctr, esc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
+  struct EvGuard {
+    cudaEvent_t a, b, c, d;
+    ~EvGuard() { for (cudaEvent_t e : {a, b, c, d}) if (e) cudaEventDestroy(e); }
+  } eg{e0, e1, e2, e3};
+  if ((rc = ctr.alloc(6 * sizeof(unsigned long long), s))) return fail(rc);
+  unsigned long long hctr[6];
+  const size_t qb = escape_rec_bytes(ts.precision);
+  for (int attempt = 0; attempt < 3; ++attempt) {
     if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
-    if (cudaMemsetAsync(ctr.p, 0, 5 * sizeof(unsigned long long), s) != cudaSuccess) {
+    if ((rc = esc.alloc(cap_q * qb, s))) return fail(rc);
+    if (cudaMemsetAsync(ctr.p, 0, 6 * sizeof(unsigned long long), s) != cudaSuccess) {
       set_error("cudaMemsetAsync failed");
       return fail(MC_ECUDA);
     }
@@ -255,7 +270,11 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     ts.capacity = cap;
     ts.cursor = ctr.as<unsigned long long>();
     ts.fates = ctr.as<unsigned long long>() + 1;
+    ts.esc = esc.p;
+    ts.esc_capacity = cap_q;
+    ts.esc_cursor = ctr.as<unsigned long long>() + 5;
     ts.records = nullptr;
+    ts.ev_mid = e3;
     cudaEventRecord(e0, s);
     if ((rc = run_transport(ts, s))) return fail(rc);
     cudaEventRecord(e1, s);
@@ -264,13 +283,21 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
       set_error("transport failed: %s", cudaGetErrorString(cudaGetLastError()));
       return fail(MC_ECUDA);
     }
-    if (hctr[0] <= cap) break;
+    if (hctr[0] <= cap && hctr[5] <= cap_q) break;
     if (hctr[0] >= 0xFFFFFFFFull) {
       set_error("%llu events exceed the 2^32 limit of one build; split the history range", hctr[0]);
       return fail(MC_EINVAL);
     }
-    cap = hctr[0];
+    // rerun with room for everything counted (a lost queue entry also lost
+    // its detections, so the event count can grow once more)
+    if (hctr[5] > cap_q) cap_q = hctr[5];
+    if (hctr[0] > cap) cap = hctr[0] + hctr[0] / 8;
+    if (attempt == 2) {
+      set_error("transport buffers kept overflowing");
+      return fail(MC_ECUDA);
+    }
   }
+  esc.release();
   sys->n_events = (int64_t)hctr[0];
   for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
   rc = assemble_system(sys, events, sys->n_events, s);
@@ -278,10 +305,12 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   if ((rc = finish_system(sys, s))) return fail(rc);
   cudaEventRecord(e2, s);
   cudaEventSynchronize(e2);
-  float t1 = 0.f, t2 = 0.f;
-  cudaEventElapsedTime(&t1, e0, e1);
+  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+  cudaEventElapsedTime(&t1, e0, e3);
+  cudaEventElapsedTime(&t3, e3, e1);
   cudaEventElapsedTime(&t2, e1, e2);
   sys->ms_transport = t1;
+  sys->ms_detect = t3;
   sys->ms_assembly = t2;
   *out = sys;
   return MC_OK;
@@ -413,6 +442,7 @@ int mc_system_info_get(const mc_system *sys, mc_system_info *info) {
   info->value_type = sys->value_type;
   info->build_ms_transport = sys->ms_transport;
   info->build_ms_assembly = sys->ms_assembly;
+  info->build_ms_detect = sys->ms_detect;
   return MC_OK;
 }
 
@@ -534,13 +564,19 @@ int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, u
   ts.key1 = (uint32_t)(seed >> 32);
   DevBuf rec, ctr;
   MCS_TRY(rec.alloc(count * sizeof(mc_history_record), s));
-  MCS_TRY(ctr.alloc(5 * sizeof(unsigned long long), s));
-  MCS_CUDA(cudaMemsetAsync(ctr.p, 0, 5 * sizeof(unsigned long long), s));
+  MCS_TRY(ctr.alloc(6 * sizeof(unsigned long long), s));
   ts.events = nullptr;
   ts.capacity = 0;
   ts.cursor = ctr.as<unsigned long long>();
   ts.fates = ctr.as<unsigned long long>() + 1;
   ts.records = rec.as<mc_history_record>();
+  DevBuf esc;
+  MCS_TRY(esc.alloc(count * escape_rec_bytes(ts.precision), s));
+  MCS_CUDA(cudaMemsetAsync(ctr.p, 0, 6 * sizeof(unsigned long long), s));
+  ts.esc = esc.p;
+  ts.esc_capacity = count;
+  ts.esc_cursor = ctr.as<unsigned long long>() + 5;
+  ts.ev_mid = nullptr;
   MCS_TRY(run_transport(ts, s));
   MCS_CUDA(cudaMemcpyAsync(out_host, rec.p, count * sizeof(mc_history_record), cudaMemcpyDeviceToHost, s));
   MCS_CUDA(cudaStreamSynchronize(s));

@@ -94,7 +94,7 @@ struct mc_system {
   uint64_t fates[4] = {0, 0, 0, 0};
   uint32_t max_count = 0;
   int32_t value_type = MC_VAL_F32;
-  double ms_transport = 0.0, ms_assembly = 0.0;
+  double ms_transport = 0.0, ms_detect = 0.0, ms_assembly = 0.0;
   // CSR (rows -> cols) and CSC (cols -> rows) of the counts C_jv
   mcs::DevBuf row_ptr, col_idx, csr_cnt;  // u32 [M+1], u32 [nnz], u32 [nnz]
   mcs::DevBuf col_ptr, row_idx, csc_cnt;  // u32 [N+1], u32 [nnz], u32 [nnz]
@@ -134,6 +134,7 @@ struct TransportSetup {
   const float *view_cs_f_dev; // [2*V] same, float
   const double *coef_d_dev;   // [3*n_mat] 0.1 rho, N_A Z/A, k Z^4 (double)
   const float *coef_f_dev;    // [3*n_mat] 0.1 rho N_A Z/A, 0.1 rho k Z^4, 0 (float)
+  const float *sig_tab_dev;   // float path: sigma_KN over the energy window
   // run
   uint64_t first, count;
   uint32_t key0, key1;
@@ -143,8 +144,15 @@ struct TransportSetup {
   unsigned long long *cursor;
   unsigned long long *fates;   // [4]
   mc_history_record *records;  // trace mode (else null)
+  void *esc;                   // escape queue (EscapeRec of the precision)
+  unsigned long long esc_capacity;
+  unsigned long long *esc_cursor;
+  cudaEvent_t ev_mid;          // recorded between transport and detection (optional)
   int precision;
 };
+
+// bytes of one escape-queue entry for a precision
+inline size_t escape_rec_bytes(int precision) { return precision == MC_FP64 ? 64 : 40; }
 
 int launch_transport(const TransportSetup &ts, cudaStream_t s);
 int launch_debug_kn(double e_kev, int precision, uint64_t seed, uint64_t n, double *cos_dev, double *eps_dev,

@@ -7,7 +7,12 @@
 // Included by transport_f32.cu (production, float) and transport_f64.cu
 // (verification, double, compiled with --fmad=false so that every product and
 // sum is rounded as written and the per-history trace can be compared with a
-// double-precision reference).
+// double-precision reference).  The double path evaluates every formula of the
+// transport contract literally (divisions, the closed-form cross-section);
+// the float path computes the same quantities with cheaper operations
+// (reciprocal multiplies, rsqrt, a cross-section table over the energy
+// window) -- the draws consumed and the decisions taken are the same, up to
+// rounding.
 //
 // One thread follows one history at a time; when its history ends it starts
 // the next one of its grid-stride sequence (lane refill), so the warps stay
@@ -18,6 +23,7 @@
 #include <cooperative_groups.h>
 
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -32,14 +38,18 @@ constexpr uint32_t kTrialCap = 10000u;    // rejection trials per scatter
 constexpr double kMec2 = 510.99895;       // electron rest energy, keV
 constexpr double kRe = 2.8179403262e-13;  // classical electron radius, cm
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kSigTab = 256;              // float path: sigma_KN table over [E_low, E0]
 
 template <typename T> struct TArgs {
   const uint8_t *mat;
   const T *coef;     // per material: double {0.1 rho, N_A Z/A, k Z^4}; float {0.1 rho N_A Z/A, 0.1 rho k Z^4}
   const T *view_cs;  // [2V] cos, sin of theta_k
+  const float *sig_tab;  // [kSigTab] sigma_KN at E_low + i (E0 - E_low)/(kSigTab - 1)
+  uint32_t rk[20];   // Philox round keys: round r uses (rk[2r], rk[2r+1])
   int nx, ny, nz, n_mat;
   T h, hx, hy, hz;   // voxel size, half extents
-  T mu_maj, e0, e_low;
+  T inv_h, hx_h, hy_h, hz_h;  // 1/h and the half extents in voxels (float path)
+  T mu_maj, inv_mu_maj, e0, e_low, inv_de;
   T ratio;           // L / d
   T w_max;           // |d_z| bound above which no view can accept (with margin)
   T start_deg, inv_delta, psi_views;  // azimuth window of candidate views
@@ -49,63 +59,177 @@ template <typename T> struct TArgs {
   uint32_t n_vox;
   uint64_t n_rows;
   uint64_t first, count;
-  uint32_t key0, key1;
   unsigned long long *events;
   unsigned long long capacity;
   unsigned long long *cursor;
   unsigned long long *fates;
   mc_history_record *records;
+  void *esc;                        // EscapeRec<T>[esc_capacity]
+  unsigned long long esc_capacity;
+  unsigned long long *esc_cursor;
 };
+
+// An escaping photon that may pass a collimator: its history, the position
+// of its random stream (words drawn so far) and its exit point and direction.
+template <typename T> struct EscapeRec {
+  uint64_t h;
+  uint32_t n_draws, pad;  // words of the history's stream used so far
+  T p[3], d[3];
+};
+static_assert(sizeof(EscapeRec<float>) == 40 && sizeof(EscapeRec<double>) == 64, "escape record layout");
+
+// Philox4x32-10 with precomputed round keys (Salmon et al., SC'11): each
+// round is two 32x32->64 multiplies and two three-way xors.
+__device__ __forceinline__ void philox_rounds(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                              const uint32_t *rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[2 * r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+}
+
+// One history's stream: block b of history h is counter (b, 0, h_lo, h_hi);
+// words are consumed w0, w1, w2, w3, then the next block.
+struct KStream {
+  uint32_t h_lo, h_hi, block, w0, w1, w2, w3, left, n_draws;
+  __device__ __forceinline__ void init(uint64_t h) {
+    h_lo = (uint32_t)h; h_hi = (uint32_t)(h >> 32);
+    block = 0; left = 0; n_draws = 0;
+  }
+  __device__ __forceinline__ uint32_t word(const uint32_t *rk) {
+    if (left == 0) {
+      uint32_t c0 = block, c1 = 0u, c2 = h_lo, c3 = h_hi;
+      philox_rounds(c0, c1, c2, c3, rk);
+      w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+      block += 1;
+      left = 4;
+    }
+    const uint32_t w = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    left -= 1;
+    n_draws += 1;
+    return w;
+  }
+};
+
+// KStream with its round keys, as a draw source.
+struct KRng {
+  KStream &s;
+  const uint32_t *rk;
+  __device__ __forceinline__ void need(uint32_t) {}
+  __device__ __forceinline__ uint32_t next() { return s.word(rk); }
+};
+
+// Per-thread ring of 16 stream words in shared memory, laid out slot-major
+// (ring[slot][thread]) so that a warp's accesses never conflict whatever slot
+// each lane is at.  ensure(k) tops the ring up (one Philox block) when fewer
+// than k words are left, and is called before each group of draws, so blocks
+// are generated where most lanes need them and no word is generated past
+// the end of a history.  The stream position is 4 * blocks - words left.
+constexpr int kRing = 16;
+constexpr int kRingThreads = 256;
+template <typename T> struct TArgs;
+struct Ring {
+  uint32_t (*buf)[kRingThreads];
+  uint32_t tid, head, avail, blk, h_lo, h_hi;
+  __device__ __forceinline__ void start(uint64_t h) {
+    h_lo = (uint32_t)h; h_hi = (uint32_t)(h >> 32);
+    blk = 0; avail = 0;
+  }
+  template <typename A> __device__ __forceinline__ void refill(const A &a) {
+    uint32_t c0 = blk, c1 = 0u, c2 = h_lo, c3 = h_hi;
+    philox_rounds(c0, c1, c2, c3, a.rk);
+    const uint32_t p = head + avail;
+    buf[p & (kRing - 1)][tid] = c0;
+    buf[(p + 1) & (kRing - 1)][tid] = c1;
+    buf[(p + 2) & (kRing - 1)][tid] = c2;
+    buf[(p + 3) & (kRing - 1)][tid] = c3;
+    avail += 4;
+    blk += 1;
+  }
+  template <typename A> __device__ __forceinline__ void ensure(uint32_t k, const A &a) {
+    if (avail < k) refill(a);
+  }
+  __device__ __forceinline__ uint32_t next() {
+    const uint32_t w = buf[head][tid];
+    head = (head + 1) & (kRing - 1);
+    avail -= 1;
+    return w;
+  }
+  __device__ __forceinline__ uint32_t n_draws() const { return 4u * blk - avail; }
+};
+
+// Ring bound to the launch's round keys, as a draw source for the samplers.
+template <typename A> struct RingRng {
+  Ring &r;
+  const A &a;
+  __device__ __forceinline__ void need(uint32_t k) { r.ensure(k, a); }
+  __device__ __forceinline__ uint32_t next() { return r.next(); }
+};
+
+template <typename T> constexpr bool is_dbl() { return std::is_same<T, double>::value; }
 
 // Klein-Nishina total cross-section per electron, cm^2, in the order
 // 2 pi re re ((1+a)/(a a) (2(1+a)/t - l/a) + l/(2a) - (1+3a)/(t t)),
 // a = E/mc^2, t = 1 + 2a, l = ln t.
-template <typename T> __device__ __forceinline__ T sigma_kn(T e) {
-  const T a = e / (T)kMec2;
-  const T t = (T)1 + (T)2 * a;
-  const T l = log(t);
-  const T term1 = ((T)1 + a) / (a * a) * ((T)2 * ((T)1 + a) / t - l / a);
-  const T term2 = l / ((T)2 * a);
-  const T term3 = ((T)1 + (T)3 * a) / (t * t);
-  return (T)(2.0 * kPi) * (T)kRe * (T)kRe * (term1 + term2 - term3);
+__device__ __forceinline__ double sigma_kn(double e) {
+  const double a = e / kMec2;
+  const double t = 1.0 + 2.0 * a;
+  const double l = log(t);
+  const double term1 = (1.0 + a) / (a * a) * (2.0 * (1.0 + a) / t - l / a);
+  const double term2 = l / (2.0 * a);
+  const double term3 = (1.0 + 3.0 * a) / (t * t);
+  return (2.0 * kPi) * kRe * kRe * (term1 + term2 - term3);
 }
 
+// Photon energy with the cross-section quantities that depend on it.
 template <typename T> struct Energy {
   T e, sig, e3, ie3;
-  __device__ __forceinline__ void set(T v) {
+  __device__ __forceinline__ void set(T v, const TArgs<T> &a, const float *tab) {
     e = v;
-    sig = sigma_kn<T>(v);
-    e3 = v * v * v;
-    if constexpr (std::is_same<T, float>::value) ie3 = 1.0f / e3;
+    if constexpr (is_dbl<T>()) {
+      sig = sigma_kn(v);
+      e3 = v * v * v;
+    } else {
+      float t = (v - a.e_low) * a.inv_de;
+      t = fminf(fmaxf(t, 0.0f), (float)(kSigTab - 1));
+      const int i = min((int)t, kSigTab - 2);
+      const float f = t - (float)i;
+      sig = fmaf(f, tab[i + 1] - tab[i], tab[i]);
+      const float ie = __fdividef(1.0f, v);
+      ie3 = ie * ie * ie;
+    }
   }
 };
 
 // mu(m, E) and mu_photo(m, E) in 1/mm.
 template <typename T>
 __device__ __forceinline__ T mu_total(const T *c0, const T *c1, const T *c2, int m, const Energy<T> &en) {
-  if constexpr (std::is_same<T, double>::value) {
-    return c0[m] * (c1[m] * en.sig + c2[m] / en.e3);
-  } else {
-    return c0[m] * en.sig + c1[m] * en.ie3;
-  }
+  if constexpr (is_dbl<T>()) return c0[m] * (c1[m] * en.sig + c2[m] / en.e3);
+  else return fmaf(c0[m], en.sig, c1[m] * en.ie3);
 }
 template <typename T>
 __device__ __forceinline__ T mu_photo(const T *c0, const T *c1, const T *c2, int m, const Energy<T> &en) {
-  if constexpr (std::is_same<T, double>::value) {
-    return c0[m] * (c2[m] / en.e3);
-  } else {
-    return c1[m] * en.ie3;
-  }
+  if constexpr (is_dbl<T>()) return c0[m] * (c2[m] / en.e3);
+  else return c1[m] * en.ie3;
 }
 
-template <typename T> __device__ __forceinline__ T neg_log(T u) {
-  if constexpr (std::is_same<T, double>::value) return -log(u);
-  else return -__logf(u);
+// Flight length -ln(u) / mu_maj.
+template <typename T> __device__ __forceinline__ T flight(T u, const TArgs<T> &a) {
+  if constexpr (is_dbl<T>()) return -log(u) / a.mu_maj;
+  else return -__logf(u) * a.inv_mu_maj;
 }
 
 // cos and sin of phi = 2 pi u.
 template <typename T> __device__ __forceinline__ void cos_sin_2pi(T u, T &c, T &s) {
-  if constexpr (std::is_same<T, double>::value) {
+  if constexpr (is_dbl<T>()) {
     const double phi = (2.0 * kPi) * u;
     c = cos(phi);
     s = sin(phi);
@@ -119,28 +243,44 @@ template <typename T> __device__ __forceinline__ void cos_sin_2pi(T u, T &c, T &
   }
 }
 
-template <typename T> __device__ __forceinline__ T voxel_index(T x, T half, T h, int n) {
-  T f = floor((x + half) / h);
-  return f > (T)(n - 1) ? (T)(n - 1) : f;
+// sqrt(max(0, x))
+template <typename T> __device__ __forceinline__ T sqrt0(T x) {
+  if constexpr (is_dbl<T>()) return sqrt(fmax(0.0, x));
+  else return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
+// Voxel index along one axis: min(floor((x + half) / h), n - 1), x >= -half.
+template <typename T> __device__ __forceinline__ int voxel_index(T x, T half, T h, T inv_h, T half_h, int n) {
+  if constexpr (is_dbl<T>()) {
+    const double f = floor((x + half) / h);
+    return (int)(f > (double)(n - 1) ? (double)(n - 1) : f);
+  } else {
+    const int i = __float2int_rd(fmaf(x, inv_h, half_h));
+    return max(0, min(i, n - 1));
+  }
 }
 
 // Compton scatter by rejection: mu uniform in [-1,1], eps = 1/(1 + a(1-mu)),
 // accepted with probability eps^2 (eps + 1/eps - (1 - mu^2)) / 2 (the
 // Klein-Nishina density over its maximum).
-template <typename T> __device__ __forceinline__ bool compton(Stream &st, T e, T &mu_out, T &eps_out) {
-  const T alpha = e / (T)kMec2;
+template <typename T, typename R>
+__device__ __forceinline__ bool compton(R &rng, T e, T &mu_out, T &eps_out) {
+  T alpha;
+  if constexpr (is_dbl<T>()) alpha = e / kMec2;
+  else alpha = e * (float)(1.0 / kMec2);
   for (uint32_t t = 0; t < kTrialCap; ++t) {
-    const T mu = (T)2 * uniform<T>(st.word()) - (T)1;
+    rng.need(2);
+    const T mu = (T)2 * uniform<T>(rng.next()) - (T)1;
     const T den = (T)1 + alpha * ((T)1 - mu);
     T eps, f;
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (is_dbl<T>()) {
       eps = 1.0 / den;
       f = 0.5 * eps * eps * (eps + 1.0 / eps - (1.0 - mu * mu));
     } else {
-      eps = __frcp_rn(den);
+      eps = __fdividef(1.0f, den);
       f = 0.5f * eps * eps * (eps + den - (1.0f - mu * mu));
     }
-    if (uniform<T>(st.word()) < f) {
+    if (uniform<T>(rng.next()) < f) {
       mu_out = mu;
       eps_out = eps;
       return true;
@@ -151,28 +291,49 @@ template <typename T> __device__ __forceinline__ bool compton(Stream &st, T e, T
 
 // Turn direction d by polar cosine mu and azimuth phi about itself.
 template <typename T> __device__ __forceinline__ void rotate(T &u, T &v, T &w, T mu, T cp, T sp) {
-  const T st = sqrt(fmax((T)0, (T)1 - mu * mu));
-  T nu, nv, nw;
-  if (fabs(w) < (T)0.99999) {
-    const T r = sqrt((T)1 - w * w);
-    nu = mu * u + st * (u * w * cp - v * sp) / r;
-    nv = mu * v + st * (v * w * cp + u * sp) / r;
-    nw = mu * w - st * cp * r;
+  if constexpr (is_dbl<T>()) {
+    const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double nu, nv, nw;
+    if (fabs(w) < 0.99999) {
+      const double r = sqrt(1.0 - w * w);
+      nu = mu * u + st * (u * w * cp - v * sp) / r;
+      nv = mu * v + st * (v * w * cp + u * sp) / r;
+      nw = mu * w - st * cp * r;
+    } else {
+      nu = st * cp;
+      nv = st * sp;
+      nw = (w >= 0.0 ? mu : -mu);
+    }
+    const double n = sqrt(nu * nu + nv * nv + nw * nw);
+    u = nu / n;
+    v = nv / n;
+    w = nw / n;
   } else {
-    nu = st * cp;
-    nv = st * sp;
-    nw = (w >= (T)0 ? mu : -mu);
+    const float st = sqrt0<float>(1.0f - mu * mu);
+    float nu, nv, nw;
+    if (fabsf(w) < 0.99999f) {
+      const float r2 = 1.0f - w * w;
+      const float ri = rsqrtf(r2);
+      const float sr = st * ri;
+      nu = fmaf(mu, u, sr * (u * w * cp - v * sp));
+      nv = fmaf(mu, v, sr * (v * w * cp + u * sp));
+      nw = fmaf(mu, w, -st * cp * (r2 * ri));
+    } else {
+      nu = st * cp;
+      nv = st * sp;
+      nw = (w >= 0.0f ? mu : -mu);
+    }
+    const float ni = rsqrtf(nu * nu + nv * nv + nw * nw);
+    u = nu * ni;
+    v = nv * ni;
+    w = nw * ni;
   }
-  const T n = sqrt(nu * nu + nv * nv + nw * nw);
-  u = nu / n;
-  v = nv / n;
-  w = nw / n;
 }
 
 struct EventSink {
   unsigned long long *events, *cursor;
   unsigned long long capacity;
-  mc_history_record *rec;  // trace mode
+  mc_history_record *rec;  // trace mode: the history's record
 };
 
 __device__ __forceinline__ void push_event(const EventSink &s, unsigned long long key) {
@@ -186,23 +347,25 @@ __device__ __forceinline__ void push_event(const EventSink &s, unsigned long lon
 
 // Offer view k to an escaping photon at p (inside the grid) moving along d.
 template <typename T, bool TRACE>
-__device__ __forceinline__ void try_view(const TArgs<T> &a, Stream &st, int k, T px, T py, T pz, T dx, T dy,
+__device__ __forceinline__ void try_view(const TArgs<T> &a, KStream &st, int k, T px, T py, T pz, T dx, T dy,
                                          T dz, uint32_t v, const EventSink &sink) {
   const T ck = a.view_cs[2 * k], sk = a.view_cs[2 * k + 1];
   const T c = dx * ck + dy * sk;
   if (!(c > (T)0)) return;
-  const T stt = sqrt(fmax((T)0, (T)1 - c * c));
+  const T stt = sqrt0<T>((T)1 - c * c);
   if (!(a.ratio * stt < c)) return;
   const T x = a.ratio * stt / c;
-  const T pass = (T)(2.0 / kPi) * (acos(x) - x * sqrt((T)1 - x * x));
-  if (!(uniform<T>(st.word()) < pass)) return;
+  const T pass = (T)(2.0 / kPi) * (acos(x) - x * sqrt0<T>((T)1 - x * x));
+  if (!(uniform<T>(st.word(a.rk)) < pass)) return;
   const T t = (a.plane - (px * ck + py * sk)) / c;
   const T qx = px + t * dx, qy = py + t * dy, qz = pz + t * dz;
   T au = -qx * sk + qy * ck;
   T bv = qz;
-  const T u1 = uniform<T>(st.word());
-  const T u2 = uniform<T>(st.word());
-  const T r = sqrt((T)2 * neg_log<T>(u1));
+  const T u1 = uniform<T>(st.word(a.rk));
+  const T u2 = uniform<T>(st.word(a.rk));
+  T r;
+  if constexpr (is_dbl<T>()) r = sqrt(-2.0 * log(u1));
+  else r = sqrt0<float>(-2.0f * __logf(u1));
   T cb, sb;
   cos_sin_2pi<T>(u2, cb, sb);
   au += a.sigma * (r * cb);
@@ -231,9 +394,8 @@ __device__ __forceinline__ int floor_div(int a, int b) {
 // the cone's half-angle), so exactly the same views are tested as in a plain
 // loop, in the same order.
 template <typename T, bool TRACE>
-__device__ void detect(const TArgs<T> &a, Stream &st, T px, T py, T pz, T dx, T dy, T dz, uint32_t v,
-                       const EventSink &sink) {
-  if (!(fabs(dz) < a.w_max)) return;
+__device__ __forceinline__ void detect(const TArgs<T> &a, KStream &st, T px, T py, T pz, T dx, T dy, T dz,
+                                       uint32_t v, const EventSink &sink) {
   const int K = a.views_per_turn;
   if (K > 0) {
     const T phi_deg = atan2(dy, dx) * (T)(180.0 / kPi);
@@ -256,65 +418,80 @@ __device__ void detect(const TArgs<T> &a, Stream &st, T px, T py, T pz, T dx, T 
 }
 
 template <typename T, bool TRACE>
-__global__ void __launch_bounds__(256) transport_kernel(const TArgs<T> a) {
+__global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_constant__ TArgs<T> a) {
   __shared__ T s_c0[256], s_c1[256], s_c2[256];
+  __shared__ float s_sig[kSigTab];
   __shared__ unsigned long long s_fates[4];
+  __shared__ uint32_t s_ring[kRing][kRingThreads];
   for (int m = threadIdx.x; m < a.n_mat; m += blockDim.x) {
     s_c0[m] = a.coef[3 * m];
     s_c1[m] = a.coef[3 * m + 1];
     s_c2[m] = a.coef[3 * m + 2];
   }
+  if (!is_dbl<T>())
+    for (int i = threadIdx.x; i < kSigTab; i += blockDim.x) s_sig[i] = a.sig_tab[i];
   if (threadIdx.x < 4) s_fates[threadIdx.x] = 0ull;
   __syncthreads();
 
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint32_t stride_mod = (uint32_t)(stride % a.n_vox);
+  // voxel of the next history, kept as (vi, vj, vk) and advanced by the
+  // stride (mod N) with carries
+  const uint32_t nx = (uint32_t)a.nx, ny = (uint32_t)a.ny, nz = (uint32_t)a.nz;
+  uint32_t vi, vj, vk, si, sj, sk;
+  {
+    const uint32_t v0 = (uint32_t)((a.first + tid) % a.n_vox);
+    vi = v0 % nx; vj = (v0 / nx) % ny; vk = v0 / (nx * ny);
+    const uint32_t sm = (uint32_t)(stride % a.n_vox);
+    si = sm % nx; sj = (sm / nx) % ny; sk = sm / (nx * ny);
+  }
   uint64_t i = tid;
-  uint32_t v = (uint32_t)((a.first + tid) % a.n_vox);  // voxel of history first + i
-  const uint32_t nxy = (uint32_t)a.nx * (uint32_t)a.ny;
 
-  Stream st;
+  Ring rg;
+  rg.buf = s_ring;
+  rg.tid = threadIdx.x;
+  rg.head = 0;
+  rg.start(a.first + i);
   T px = 0, py = 0, pz = 0, dx = 0, dy = 0, dz = 1;
   Energy<T> en;
   en.e = en.sig = en.e3 = en.ie3 = (T)0;
+  Energy<T> en0;
+  en0.set(a.e0, a, s_sig);
   uint32_t steps = 0, n_virtual = 0, n_real = 0, n_compton = 0;
-  uint32_t cur_v = 0;
   uint64_t cur_i = 0;
   bool alive = false;
-  mc_history_record rec;
-  EventSink sink{a.events, a.cursor, a.capacity, &rec};
+  uint32_t n_fate[4] = {0u, 0u, 0u, 0u};  // fates of this thread's histories
 
+  RingRng<TArgs<T>> rng{rg, a};
   for (;;) {
+    if (!alive && i >= a.count) break;
     int fate = -1;
     if (!alive) {
-      if (i >= a.count) break;
-      // emission (Sec. 3, isotropic 4 pi): uniform point in voxel v, uniform direction
+      // emission (Sec. 3, isotropic 4 pi): uniform point in voxel v, uniform
+      // direction; five draws
+      rg.ensure(4, a);
       cur_i = i;
-      cur_v = v;
-      st.init(a.key0, a.key1, a.first + i);
+      px = ((T)vi + uniform<T>(rg.next())) * a.h - a.hx;
+      py = ((T)vj + uniform<T>(rg.next())) * a.h - a.hy;
+      pz = ((T)vk + uniform<T>(rg.next())) * a.h - a.hz;
       i += stride;
-      v += stride_mod;
-      if (v >= a.n_vox) v -= a.n_vox;
-      const uint32_t vi = cur_v % (uint32_t)a.nx;
-      const uint32_t vj = (cur_v / (uint32_t)a.nx) % (uint32_t)a.ny;
-      const uint32_t vk = cur_v / nxy;
-      px = ((T)vi + uniform<T>(st.word())) * a.h - a.hx;
-      py = ((T)vj + uniform<T>(st.word())) * a.h - a.hy;
-      pz = ((T)vk + uniform<T>(st.word())) * a.h - a.hz;
-      const T ct = (T)2 * uniform<T>(st.word()) - (T)1;
+      vi += si;
+      if (vi >= nx) { vi -= nx; vj += 1; }
+      vj += sj;
+      if (vj >= ny) { vj -= ny; vk += 1; }
+      vk += sk;
+      if (vk >= nz) vk -= nz;
+      const T ct = (T)2 * uniform<T>(rg.next()) - (T)1;
+      rg.ensure(1, a);
       T cph, sph;
-      cos_sin_2pi<T>(uniform<T>(st.word()), cph, sph);
-      const T sth = sqrt(fmax((T)0, (T)1 - ct * ct));
+      cos_sin_2pi<T>(uniform<T>(rg.next()), cph, sph);
+      const T sth = sqrt0<T>((T)1 - ct * ct);
       dx = sth * cph;
       dy = sth * sph;
       dz = ct;
-      en.set(a.e0);
+      en = en0;
       steps = n_virtual = n_real = n_compton = 0;
       alive = true;
-      if (TRACE) {
-        rec.n_events = 0;
-      }
       if (!(a.mu_maj > (T)0)) fate = MC_FATE_ESCAPE;
     }
     if (fate < 0) {
@@ -323,28 +500,31 @@ __global__ void __launch_bounds__(256) transport_kernel(const TArgs<T> a) {
         fate = MC_FATE_CAP;
       } else {
         steps += 1;
-        const T s = neg_log<T>(uniform<T>(st.word())) / a.mu_maj;
+        rg.ensure(2, a);  // the flight and its real/virtual test
+        const T s = flight<T>(uniform<T>(rg.next()), a);
         const T qx = px + s * dx, qy = py + s * dy, qz = pz + s * dz;
         if (!(qx >= -a.hx && qx < a.hx && qy >= -a.hy && qy < a.hy && qz >= -a.hz && qz < a.hz)) {
           fate = MC_FATE_ESCAPE;  // leaves from the pre-flight point p
         } else {
           px = qx; py = qy; pz = qz;
-          const int ix = (int)voxel_index<T>(px, a.hx, a.h, a.nx);
-          const int iy = (int)voxel_index<T>(py, a.hy, a.h, a.ny);
-          const int iz = (int)voxel_index<T>(pz, a.hz, a.h, a.nz);
+          const int ix = voxel_index<T>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
+          const int iy = voxel_index<T>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
+          const int iz = voxel_index<T>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
           const int m = __ldg(a.mat + ((size_t)iz * a.ny + iy) * a.nx + ix);
           const T mu = mu_total<T>(s_c0, s_c1, s_c2, m, en);
-          if (uniform<T>(st.word()) * a.mu_maj < mu) {
+          if (uniform<T>(rg.next()) * a.mu_maj < mu) {
             n_real += 1;
-            if (uniform<T>(st.word()) * mu < mu_photo<T>(s_c0, s_c1, s_c2, m, en)) {
+            rg.ensure(1, a);
+            if (uniform<T>(rg.next()) * mu < mu_photo<T>(s_c0, s_c1, s_c2, m, en)) {
               fate = MC_FATE_ABSORBED;
             } else {
               T mu_c, eps;
-              if (!compton<T>(st, en.e, mu_c, eps)) {
+              if (!compton<T>(rng, en.e, mu_c, eps)) {
                 fate = MC_FATE_CAP;
               } else {
+                rg.ensure(1, a);
                 T cp, sp;
-                cos_sin_2pi<T>(uniform<T>(st.word()), cp, sp);
+                cos_sin_2pi<T>(uniform<T>(rg.next()), cp, sp);
                 rotate<T>(dx, dy, dz, mu_c, cp, sp);
                 const T e_new = eps * en.e;
                 n_compton += 1;
@@ -352,7 +532,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const TArgs<T> a) {
                   en.e = e_new;
                   fate = MC_FATE_BELOW_WINDOW;
                 } else {
-                  en.set(e_new);
+                  en.set(e_new, a, s_sig);
                 }
               }
             }
@@ -363,35 +543,100 @@ __global__ void __launch_bounds__(256) transport_kernel(const TArgs<T> a) {
       }
     }
     if (fate >= 0) {
-      if (fate == MC_FATE_ESCAPE) detect<T, TRACE>(a, st, px, py, pz, dx, dy, dz, cur_v, sink);
-      atomicAdd(&s_fates[fate], 1ull);
+      if (fate == MC_FATE_ESCAPE && fabs(dz) < a.w_max) {
+        // a view may accept it: queue it for the detection kernel
+        cg::coalesced_group g = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (g.thread_rank() == 0) base = atomicAdd(a.esc_cursor, (unsigned long long)g.size());
+        base = g.shfl(base, 0);
+        const unsigned long long q = base + g.thread_rank();
+        if (q < a.esc_capacity) {
+          EscapeRec<T> e;
+          e.h = a.first + cur_i;
+          e.n_draws = rg.n_draws();
+          e.pad = 0;
+          e.p[0] = px; e.p[1] = py; e.p[2] = pz;
+          e.d[0] = dx; e.d[1] = dy; e.d[2] = dz;
+          static_cast<EscapeRec<T> *>(a.esc)[q] = e;
+        }
+      }
+      n_fate[0] += fate == 0;
+      n_fate[1] += fate == 1;
+      n_fate[2] += fate == 2;
+      n_fate[3] += fate == 3;
       if (TRACE) {
+        mc_history_record rec;
         rec.fate = (uint8_t)fate;
+        rec.n_events = 0;
         rec.pad = 0;
         rec.n_virtual = n_virtual;
         rec.n_real = n_real;
         rec.n_compton = n_compton;
-        rec.n_draws = st.n_draws;
+        rec.n_draws = rg.n_draws();
         rec.pad2 = 0;
         rec.e_final_kev = (double)en.e;
-        for (int e = rec.n_events; e < 4; ++e) rec.event_row[e] = 0;
+        for (int e = 0; e < 4; ++e) rec.event_row[e] = 0;
         a.records[cur_i] = rec;
       }
       alive = false;
+      rg.start(a.first + i);  // next history's stream (unused past the end)
     }
+  }
+  // fates: warp sums, then one shared atomic per warp and fate
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    unsigned long long c = n_fate[f];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_fates[f], c);
   }
   __syncthreads();
   if (threadIdx.x < 4 && s_fates[threadIdx.x]) atomicAdd(&a.fates[threadIdx.x], s_fates[threadIdx.x]);
 }
 
+// Detection of the queued escapes (Sec. 3): each thread resumes one
+// photon's random stream where transport left it and offers the photon to the
+// views.  Trace mode adds the detections and draws to the history's record.
+template <typename T, bool TRACE>
+__global__ void __launch_bounds__(256) detect_kernel(const __grid_constant__ TArgs<T> a) {
+  const unsigned long long n_q = *a.esc_cursor < a.esc_capacity ? *a.esc_cursor : a.esc_capacity;
+  const EscapeRec<T> *q = static_cast<const EscapeRec<T> *>(a.esc);
+  for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_q;
+       e += (unsigned long long)gridDim.x * blockDim.x) {
+    const EscapeRec<T> r = q[e];
+    KStream st;
+    st.init(r.h);
+    const uint32_t b = r.n_draws >> 2, used = r.n_draws & 3u;
+    st.block = b;
+    st.left = 0;
+    if (used > 0) {
+      uint32_t c0 = b, c1 = 0u, c2 = st.h_lo, c3 = st.h_hi;
+      philox_rounds(c0, c1, c2, c3, a.rk);
+      // the block's words not drawn yet
+      if (used == 1) { st.w0 = c1; st.w1 = c2; st.w2 = c3; }
+      else if (used == 2) { st.w0 = c2; st.w1 = c3; }
+      else { st.w0 = c3; }
+      st.left = 4 - used;
+      st.block = b + 1;
+    }
+    st.n_draws = r.n_draws;
+    const uint32_t v = (uint32_t)(r.h % a.n_vox);
+    mc_history_record *rec = TRACE ? a.records + (r.h - a.first) : nullptr;
+    EventSink sink{a.events, a.cursor, a.capacity, rec};
+    detect<T, TRACE>(a, st, r.p[0], r.p[1], r.p[2], r.d[0], r.d[1], r.d[2], v, sink);
+    if (TRACE) rec->n_draws = st.n_draws;
+  }
+}
+
 // Compton sampler alone (verification).
 template <typename T>
-__global__ void debug_kn_kernel(T e, uint32_t k0, uint32_t k1, uint64_t n, double *cos_out, double *eps_out) {
+__global__ void debug_kn_kernel(const __grid_constant__ TArgs<T> a, T e, uint64_t n, double *cos_out, double *eps_out) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    Stream st;
-    st.init(k0, k1, i);
+    KStream st;
+    st.init(i);
+    KRng rng{st, a.rk};
     T mu = 0, eps = 0;
-    compton<T>(st, e, mu, eps);
+    compton<T>(rng, e, mu, eps);
     cos_out[i] = (double)mu;
     eps_out[i] = (double)eps;
   }
@@ -400,33 +645,36 @@ __global__ void debug_kn_kernel(T e, uint32_t k0, uint32_t k1, uint64_t n, doubl
 // Woodcock flight alone (verification): photons from p0 along d, counts
 // those that leave the grid without a real collision.
 template <typename T>
-__global__ void debug_beam_kernel(const TArgs<T> a, T p0x, T p0y, T p0z, T dx, T dy, T dz, T e, uint64_t n,
-                                  unsigned long long *through) {
+__global__ void debug_beam_kernel(const __grid_constant__ TArgs<T> a, T p0x, T p0y, T p0z, T dx, T dy, T dz, T e,
+                                  uint64_t n, unsigned long long *through) {
   __shared__ T s_c0[256], s_c1[256], s_c2[256];
+  __shared__ float s_sig[kSigTab];
   for (int m = threadIdx.x; m < a.n_mat; m += blockDim.x) {
     s_c0[m] = a.coef[3 * m];
     s_c1[m] = a.coef[3 * m + 1];
     s_c2[m] = a.coef[3 * m + 2];
   }
+  if (!is_dbl<T>())
+    for (int i = threadIdx.x; i < kSigTab; i += blockDim.x) s_sig[i] = a.sig_tab[i];
   __syncthreads();
   Energy<T> en;
-  en.set(e);
+  en.set(e, a, s_sig);
   unsigned long long mine = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     if (!(a.mu_maj > (T)0)) { mine += 1; continue; }
-    Stream st;
-    st.init(a.key0, a.key1, i);
+    KStream st;
+    st.init(i);
     T px = p0x, py = p0y, pz = p0z;
     for (uint32_t s = 0; s < kStepCap; ++s) {
-      const T l = neg_log<T>(uniform<T>(st.word())) / a.mu_maj;
+      const T l = flight<T>(uniform<T>(st.word(a.rk)), a);
       const T qx = px + l * dx, qy = py + l * dy, qz = pz + l * dz;
       if (!(qx >= -a.hx && qx < a.hx && qy >= -a.hy && qy < a.hy && qz >= -a.hz && qz < a.hz)) { mine += 1; break; }
       px = qx; py = qy; pz = qz;
-      const int ix = (int)voxel_index<T>(px, a.hx, a.h, a.nx);
-      const int iy = (int)voxel_index<T>(py, a.hy, a.h, a.ny);
-      const int iz = (int)voxel_index<T>(pz, a.hz, a.h, a.nz);
+      const int ix = voxel_index<T>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
+      const int iy = voxel_index<T>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
+      const int iz = voxel_index<T>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
       const int m = a.mat[((size_t)iz * a.ny + iy) * a.nx + ix];
-      if (uniform<T>(st.word()) * a.mu_maj < mu_total<T>(s_c0, s_c1, s_c2, m, en)) break;
+      if (uniform<T>(st.word(a.rk)) * a.mu_maj < mu_total<T>(s_c0, s_c1, s_c2, m, en)) break;
     }
   }
   if (mine) atomicAdd(through, mine);
@@ -485,20 +733,45 @@ inline void host_coefficients(const TransportSetup &ts, std::vector<double> &cd,
   }
 }
 
+inline void round_keys(uint32_t key0, uint32_t key1, uint32_t rk[20]) {
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = key0 + (uint32_t)r * 0x9E3779B9u;
+    rk[2 * r + 1] = key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
+
+// float path: sigma_KN tabulated at E_low + i (E0 - E_low) / (kSigTab - 1)
+inline void host_sigma_table(const TransportSetup &ts, std::vector<float> &tab) {
+  const double el = host_e_low(ts), de = (ts.e0 - el) / (kSigTab - 1);
+  tab.resize(kSigTab);
+  for (int i = 0; i < kSigTab; ++i) tab[i] = (float)host_sigma_kn(el + i * de);
+}
+
 template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
+  std::memset(&a, 0, sizeof(a));
   a.coef = std::is_same<T, double>::value ? (const T *)(const void *)ts.coef_d_dev
                                           : (const T *)(const void *)ts.coef_f_dev;
   a.mat = ts.material_dev;
   a.view_cs = std::is_same<T, double>::value ? (const T *)(const void *)ts.view_cs_dev
                                              : (const T *)(const void *)ts.view_cs_f_dev;
+  a.sig_tab = ts.sig_tab_dev;
+  round_keys(ts.key0, ts.key1, a.rk);
   a.nx = ts.nx; a.ny = ts.ny; a.nz = ts.nz; a.n_mat = ts.n_mat;
   a.h = (T)ts.h;
   a.hx = (T)(0.5 * ts.nx * ts.h);
   a.hy = (T)(0.5 * ts.ny * ts.h);
   a.hz = (T)(0.5 * ts.nz * ts.h);
-  a.mu_maj = (T)host_majorant(ts);
+  a.inv_h = (T)(1.0 / ts.h);
+  a.hx_h = (T)(0.5 * ts.nx);
+  a.hy_h = (T)(0.5 * ts.ny);
+  a.hz_h = (T)(0.5 * ts.nz);
+  const double maj = host_majorant(ts);
+  a.mu_maj = (T)maj;
+  a.inv_mu_maj = (T)(maj > 0.0 ? 1.0 / maj : 0.0);
   a.e0 = (T)ts.e0;
-  a.e_low = (T)host_e_low(ts);
+  const double el = host_e_low(ts);
+  a.e_low = (T)el;
+  a.inv_de = (T)((kSigTab - 1) / (ts.e0 - el));
   const double ratio = ts.hole_len / ts.hole_diam;
   a.ratio = (T)ratio;
   const double tan_max = ts.hole_diam / ts.hole_len;
@@ -522,9 +795,11 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.n_vox = (uint32_t)((uint64_t)ts.nx * ts.ny * ts.nz);
   a.n_rows = (uint64_t)ts.n_views * ts.bins_u * ts.bins_v;
   a.first = ts.first; a.count = ts.count;
-  a.key0 = ts.key0; a.key1 = ts.key1;
   a.events = ts.events; a.capacity = ts.capacity; a.cursor = ts.cursor; a.fates = ts.fates;
   a.records = ts.records;
+  a.esc = ts.esc;
+  a.esc_capacity = ts.esc_capacity;
+  a.esc_cursor = ts.esc_cursor;
 }
 
 template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStream_t s) {
@@ -545,16 +820,24 @@ template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStrea
   if (ts.records) { count_launch(); transport_kernel<T, true><<<grid, threads, 0, s>>>(a); }
   else { count_launch(); transport_kernel<T, false><<<grid, threads, 0, s>>>(a); }
   MCS_LAUNCHED();
+  if (ts.ev_mid) MCS_CUDA(cudaEventRecord(ts.ev_mid, s));
+  const int dgrid = device_sm_count() * 8;
+  if (ts.records) { count_launch(); detect_kernel<T, true><<<dgrid, 256, 0, s>>>(a); }
+  else { count_launch(); detect_kernel<T, false><<<dgrid, 256, 0, s>>>(a); }
+  MCS_LAUNCHED();
   return MC_OK;
 }
 
 template <typename T>
 int launch_debug_kn_t(double e_kev, uint64_t seed, uint64_t n, double *cos_dev, double *eps_dev, cudaStream_t s) {
   if (n == 0) return MC_OK;
+  TArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  round_keys((uint32_t)seed, (uint32_t)(seed >> 32), a.rk);
   const int threads = 256;
   const int64_t need = (int64_t)((n + threads - 1) / threads);
   const int grid = (int)(need < 4096 ? need : 4096);
-  count_launch(); debug_kn_kernel<T><<<grid, threads, 0, s>>>((T)e_kev, (uint32_t)seed, (uint32_t)(seed >> 32), n, cos_dev, eps_dev);
+  count_launch(); debug_kn_kernel<T><<<grid, threads, 0, s>>>(a, (T)e_kev, n, cos_dev, eps_dev);
   MCS_LAUNCHED();
   return MC_OK;
 }

@@ -3,8 +3,10 @@
 #include "transport.cuh"
 
 namespace mcs {
-void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf) {
+void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
+                          std::vector<float> &sig_tab) {
   host_coefficients(ts, cd, cf);
+  host_sigma_table(ts, sig_tab);
 }
 int launch_transport_f32(const TransportSetup &ts, cudaStream_t s) { return launch_transport_t<float>(ts, s); }
 int launch_debug_kn_f32(double e, uint64_t seed, uint64_t n, double *c, double *p, cudaStream_t s) {

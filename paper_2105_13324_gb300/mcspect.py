@@ -67,7 +67,7 @@ class MCSystemInfo(ctypes.Structure):
                 ("n_events", ctypes.c_int64), ("first_history", ctypes.c_uint64),
                 ("n_histories", ctypes.c_uint64), ("fates", ctypes.c_uint64 * 4), ("max_count", ctypes.c_uint32),
                 ("value_type", ctypes.c_int32), ("build_ms_transport", ctypes.c_double),
-                ("build_ms_assembly", ctypes.c_double)]
+                ("build_ms_assembly", ctypes.c_double), ("build_ms_detect", ctypes.c_double)]
 
 
 _lib = None
@@ -185,7 +185,7 @@ class System:
                 "first_history": inf.first_history, "n_histories": inf.n_histories,
                 "fates": [int(v) for v in inf.fates], "max_count": inf.max_count,
                 "value_type": inf.value_type, "build_ms_transport": inf.build_ms_transport,
-                "build_ms_assembly": inf.build_ms_assembly}
+                "build_ms_assembly": inf.build_ms_assembly, "build_ms_detect": inf.build_ms_detect}
 
     @property
     def shape(self):
