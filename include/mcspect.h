@@ -201,6 +201,27 @@ MC_API int mc_mlem_init(mc_system *sys, const float *y_dev, float *x_dev, void *
 MC_API int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter, double *loglik_host,
                  void *stream);
 
+/* ML-EM like mlem_iterate, for callers that must not allocate device
+ * memory: a reconstruction service that plans its memory up front (a device
+ * allocation or free can synchronise the whole device and stall concurrent
+ * work, or fail under a fixed memory cap), or host code whose device memory
+ * is owned by another allocator.  mlem_iterate may allocate its
+ * log-likelihood buffer on first use; this entry point never calls
+ * cudaMalloc, cudaFree or any allocating routine.  The paper has no
+ * counterpart: it is a deployment variant of Eq. (MLEM).
+ *
+ * Its work vectors live in one static device array of ~18 MiB that every GPU
+ * loading the library keeps until the process exits.  Limits: n_rows and
+ * n_cols at most 2^21 each (2,097,152) and at most 4096 log-likelihood
+ * values per call; larger requests return MC_EINVAL with a message.  The
+ * first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  All calls on
+ * a device share the array and leave their values in it: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Results equal mlem_iterate's on the same inputs. */
+MC_API int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter,
+                                double *loglik_host, void *stream);
+
 /* Verification: per-history trace records of histories first ..
  * first+count-1 (records written to out_host[count]).  Synchronises. */
 MC_API int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,

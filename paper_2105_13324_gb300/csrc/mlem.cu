@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace mcs {
@@ -273,3 +275,100 @@ int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll,
 }
 
 }  // namespace mcs
+
+// ---------------------------------------------------------------------------
+// ML-EM without any device allocation
+// ---------------------------------------------------------------------------
+// Scratch of mlem_iterate_noalloc lives in this file-scope device array: one
+// copy per GPU that loads the library, held until the process exits.  It
+// holds the ratio vector r (M floats), the scaled image xs (N floats), the
+// per-block log-likelihood partials and the per-iteration log-likelihoods.
+namespace mcs {
+constexpr int64_t kNoAllocRows = int64_t(1) << 21;   // largest M
+constexpr int64_t kNoAllocCols = int64_t(1) << 21;   // largest N
+constexpr int64_t kNoAllocPartials = kNoAllocRows * 32 / kSpmvThreads;  // forward blocks at 32 lanes/row
+constexpr int64_t kNoAllocIters = 4096;              // log-likelihood values per call
+constexpr size_t kNoAllocOffR = 0;
+constexpr size_t kNoAllocOffXs = kNoAllocOffR + sizeof(float) * kNoAllocRows;
+constexpr size_t kNoAllocOffPart = kNoAllocOffXs + sizeof(float) * kNoAllocCols;
+constexpr size_t kNoAllocOffLl = kNoAllocOffPart + sizeof(double) * kNoAllocPartials;
+constexpr size_t kNoAllocBytes = kNoAllocOffLl + sizeof(double) * kNoAllocIters;  // ~18 MiB
+
+static __device__ __align__(256) unsigned char g_mlem_scratch[kNoAllocBytes];
+
+// Device address of g_mlem_scratch on the current device (host code may not
+// use the symbol itself: on the host it names a stand-in, not device memory).
+static int noalloc_scratch(unsigned char **out) {
+  static std::mutex mu;
+  static void *addr[256] = {};
+  int dev = 0;
+  MCS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) { set_error("device ordinal %d out of range", dev); return MC_EINVAL; }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    MCS_CUDA(cudaGetSymbolAddress(&p, g_mlem_scratch));
+    addr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(addr[dev]);
+  return MC_OK;
+}
+}  // namespace mcs
+
+extern "C" int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter,
+                                    double *loglik_host, void *stream) {
+  using namespace mcs;
+  clear_error();
+  if (!sys || !y_dev || !x_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  if (n_iter < 0) { set_error("n_iter must be >= 0"); return MC_EINVAL; }
+  if (sys->n_rows > kNoAllocRows || sys->n_cols > kNoAllocCols) {
+    set_error("mlem_iterate_noalloc: system of %lld rows x %lld columns exceeds the static scratch limit of "
+              "%lld rows x %lld columns; use mlem_iterate",
+              (long long)sys->n_rows, (long long)sys->n_cols, (long long)kNoAllocRows, (long long)kNoAllocCols);
+    return MC_EINVAL;
+  }
+  const bool want = loglik_host != nullptr && n_iter > 0;
+  if (want && n_iter > kNoAllocIters) {
+    set_error("mlem_iterate_noalloc: at most %lld log-likelihood values per call", (long long)kNoAllocIters);
+    return MC_EINVAL;
+  }
+  const int fb = forward_blocks(sys);
+  if (fb > kNoAllocPartials) {
+    set_error("mlem_iterate_noalloc: %d forward blocks exceed the static limit %lld", fb, (long long)kNoAllocPartials);
+    return MC_EINVAL;
+  }
+  unsigned char *base = nullptr;
+  MCS_TRY(noalloc_scratch(&base));
+  float *r = reinterpret_cast<float *>(base + kNoAllocOffR);
+  float *xs = reinterpret_cast<float *>(base + kNoAllocOffXs);
+  double *partials = reinterpret_cast<double *>(base + kNoAllocOffPart);
+  double *ll = reinterpret_cast<double *>(base + kNoAllocOffLl);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t m = sys->n_rows, n = sys->n_cols;
+  // every scratch element is written before it is read: nothing to clear
+  if (n > 0) {
+    count_launch();
+    prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x_dev, sys->inv_n.as<float>(), xs, n);
+  }
+  MCS_LAUNCHED();
+  for (int k = 0; k < n_iter; ++k) {
+    if (m > 0) {
+      if (want) {
+        fwd_dispatch<1, true>(sys, xs, y_dev, r, partials, s);
+        count_launch();
+        sum_partials_kernel<<<1, 1024, 0, s>>>(partials, fb, ll + k);
+      } else {
+        fwd_dispatch<1, false>(sys, xs, y_dev, r, nullptr, s);
+      }
+    } else if (want) {
+      MCS_CUDA(cudaMemsetAsync(ll + k, 0, sizeof(double), s));
+    }
+    if (n > 0) back_dispatch<1>(sys, r, x_dev, xs, s);
+    MCS_LAUNCHED();
+  }
+  if (want) {
+    MCS_CUDA(cudaMemcpyAsync(loglik_host, ll, (size_t)n_iter * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaStreamSynchronize(s));
+  }
+  return MC_OK;
+}

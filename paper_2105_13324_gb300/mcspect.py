@@ -29,7 +29,7 @@ FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 EXPORTED = (
     "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
-    "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate",
+    "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
 )
 
@@ -102,6 +102,7 @@ def load(path: str | None = None):
             "mc_sensitivity": [vp, vp, vp],
             "mc_mlem_init": [vp, vp, vp, vp],
             "mlem_iterate": [vp, vp, vp, i32, vp, vp],
+            "mlem_iterate_noalloc": [vp, vp, vp, i32, vp, vp],
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
             "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
@@ -338,6 +339,15 @@ def mlem_iterate(sys: System, y, x, n_iter: int, loglik: bool = False, stream=No
     ll = np.zeros(max(n_iter, 1), np.float64) if loglik else None
     _check(load().mlem_iterate(sys.handle, _dev_ptr(y, torch.float32), _dev_ptr(x, torch.float32), int(n_iter),
                                ll.ctypes.data if loglik else None, _stream_ptr(stream)))
+    return ll[:n_iter] if loglik else None
+
+
+def mlem_iterate_noalloc(sys: System, y, x, n_iter: int, loglik: bool = False, stream=None):
+    """mlem_iterate without device allocation (static scratch, size-limited)."""
+    import torch
+    ll = np.zeros(max(n_iter, 1), np.float64) if loglik else None
+    _check(load().mlem_iterate_noalloc(sys.handle, _dev_ptr(y, torch.float32), _dev_ptr(x, torch.float32),
+                                       int(n_iter), ll.ctypes.data if loglik else None, _stream_ptr(stream)))
     return ll[:n_iter] if loglik else None
 
 
