@@ -133,11 +133,19 @@ __global__ void init_sums_kernel(const float *y, int64_t m, const double *colsum
   if (threadIdx.x == 0) { py[blockIdx.x] = ty; ps[blockIdx.x] = ts; }
 }
 
-__global__ void init_fill_kernel(const double *py, const double *ps, int nb, const double *colsum,
-                                 const float *inv_n, int64_t n, float *x, float *xs) {
-  double sy = 0.0, ss = 0.0;
-  for (int b = 0; b < nb; ++b) { sy += py[b]; ss += ps[b]; }
-  const float x0 = ss > 0.0 ? (float)(sy / ss) : 0.0f;
+// x0 = sum(y) / sum(s) from the block partials (one block, fixed order)
+__global__ void init_total_kernel(const double *py, const double *ps, int nb, double *x0) {
+  __shared__ double s_tmp[32];
+  double ay = 0.0, as = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) { ay += py[b]; as += ps[b]; }
+  const double sy = block_sum_double(ay, s_tmp);
+  const double ss = block_sum_double(as, s_tmp);
+  if (threadIdx.x == 0) *x0 = ss > 0.0 ? sy / ss : 0.0;
+}
+
+__global__ void init_fill_kernel(const double *x0p, const double *colsum, const float *inv_n, int64_t n, float *x,
+                                 float *xs) {
+  const float x0 = (float)*x0p;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const float xv = colsum[v] > 0.0 ? x0 : 0.0f;
     x[v] = xv;
@@ -214,9 +222,10 @@ static void back_dispatch(const mc_system *sys, const float *r, float *x, float 
 int forward_blocks(const mc_system *sys) { return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads); }
 
 int project(const mc_system *sys, const float *x, float *q, cudaStream_t s) {
-  if (sys->n_cols > 0)
+  if (sys->n_cols > 0) {
     count_launch(); prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
                                                                      sys->n_cols);
+  }
   if (sys->n_rows > 0) fwd_dispatch<0, false>(sys, sys->xs.as<float>(), nullptr, q, nullptr, s);
   MCS_LAUNCHED();
   return MC_OK;
@@ -229,9 +238,10 @@ int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s) 
 }
 
 int sensitivity(const mc_system *sys, double *out, cudaStream_t s) {
-  if (sys->n_cols > 0)
+  if (sys->n_cols > 0) {
     count_launch(); sensitivity_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(sys->colsum.as<double>(),
                                                                        sys->n_v.as<uint32_t>(), sys->n_cols, out);
+  }
   MCS_LAUNCHED();
   return MC_OK;
 }
@@ -239,22 +249,29 @@ int sensitivity(const mc_system *sys, double *out, cudaStream_t s) {
 int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s) {
   const int nb = 256;
   DevBuf part;
-  MCS_TRY(part.alloc(2 * nb * sizeof(double), s));
-  count_launch(); init_sums_kernel<<<nb, 256, 0, s>>>(y, sys->n_rows, sys->colsum.as<double>(), sys->n_v.as<uint32_t>(), sys->n_cols,
-                                      part.as<double>(), part.as<double>() + nb);
+  MCS_TRY(part.alloc((2 * nb + 1) * sizeof(double), s));
+  double *py = part.as<double>(), *ps = py + nb, *x0 = py + 2 * nb;
+  count_launch();
+  init_sums_kernel<<<nb, 256, 0, s>>>(y, sys->n_rows, sys->colsum.as<double>(), sys->n_v.as<uint32_t>(), sys->n_cols,
+                                      py, ps);
+  count_launch();
+  init_total_kernel<<<1, 256, 0, s>>>(py, ps, nb, x0);
   MCS_LAUNCHED();
-  if (sys->n_cols > 0)
-    count_launch(); init_fill_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(part.as<double>(), part.as<double>() + nb, nb,
-                                                                     sys->colsum.as<double>(), sys->inv_n.as<float>(),
-                                                                     sys->n_cols, x, sys->xs.as<float>());
+  if (sys->n_cols > 0) {
+    count_launch();
+    init_fill_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x0, sys->colsum.as<double>(),
+                                                                     sys->inv_n.as<float>(), sys->n_cols, x,
+                                                                     sys->xs.as<float>());
+  }
   MCS_LAUNCHED();
   return MC_OK;
 }
 
 int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll, cudaStream_t s) {
   const int64_t m = sys->n_rows, n = sys->n_cols;
-  if (n > 0)
+  if (n > 0) {
     count_launch(); prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(), n);
+  }
   MCS_LAUNCHED();
   const int fb = forward_blocks(sys);
   for (int k = 0; k < n_iter; ++k) {
