@@ -201,9 +201,11 @@ static int run_transport(const TransportSetup &ts, cudaStream_t s) {
   return ts.precision == MC_FP64 ? launch_transport_f64(ts, s) : launch_transport_f32(ts, s);
 }
 
+// Lanes per row (column) of the row-group kernels: about 8 entries per lane
+// (two 4-entry vector steps), at most a warp.
 static int pick_group(double mean_len) {
   int g = 1;
-  while (g < 32 && g < mean_len) g <<= 1;
+  while (g < 32 && 8 * g < mean_len) g <<= 1;
   return g;
 }
 
@@ -214,10 +216,18 @@ static int finish_system(mc_system *sys, cudaStream_t s) {
   MCS_TRY(sys->r.alloc((size_t)(sys->n_rows > 0 ? sys->n_rows : 1) * sizeof(float), s));
   sys->spmv_group_fwd = pick_group(sys->n_rows > 0 ? (double)sys->nnz / sys->n_rows : 1.0);
   sys->spmv_group_bwd = pick_group(sys->n_cols > 0 ? (double)sys->nnz / sys->n_cols : 1.0);
+  MCS_TRY(make_stream_blocks(sys, s));
   const int fb = forward_blocks(sys);
   MCS_TRY(sys->partials.alloc((size_t)(fb > 0 ? fb : 1) * sizeof(double), s));
   MCS_CUDA(cudaStreamSynchronize(s));
   return MC_OK;
+}
+
+constexpr int kCounters = 7;  // events, fates[4], queue fill, largest queue fill
+
+__global__ void queue_reset_kernel(unsigned long long *ctr) {
+  if (ctr[5] > ctr[6]) ctr[6] = ctr[5];
+  ctr[5] = 0ull;
 }
 
 static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
@@ -237,32 +247,39 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   sys->first = first;
   sys->count = count;
   int rc;
-  // Event capacity: the unattenuated per-view acceptance (d/L)^2/16 per
-  // history, 25 % headroom.  Escape-queue capacity: an isotropic photon has
-  // |d_z| below the collimator's acceptance bound with probability ~w_max.
-  // Both are rerun with the exact sizes if they overflow.
+  // Histories run in chunks of kChunk: the escape queue is sized for one
+  // chunk and reused, the events of all chunks accumulate.  Event capacity:
+  // the unattenuated per-view acceptance (d/L)^2/16 per history, 25 %
+  // headroom.  Queue capacity: an isotropic photon has |d_z| below the
+  // collimator's acceptance bound with probability ~w_max.  Both are rerun
+  // with the exact sizes if they overflow (transport is deterministic).
+  const uint64_t kChunk = 1ull << 27;
+  const uint64_t n_chunks = (count + kChunk - 1) / kChunk;
+  const uint64_t chunk_max = count < kChunk ? count : kChunk;
   const double tan_max = ts.hole_diam / ts.hole_len;
   const double acc = tan_max * tan_max / 16.0;
   double est = (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
   if (est > 4.0e9) est = 4.0e9;
   const double w_max = tan_max / std::sqrt(1.0 + tan_max * tan_max) * 1.02 + 1e-6;
-  double est_q = (double)count * w_max * 1.1 + 65536.0;
-  if (est_q > (double)count) est_q = (double)count;
+  double est_q = (double)chunk_max * w_max * 1.1 + 65536.0;
+  if (est_q > (double)chunk_max) est_q = (double)chunk_max;
   unsigned long long cap = (unsigned long long)est, cap_q = (unsigned long long)est_q;
   DevBuf events, ctr, esc;
-  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
-  cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3);
+  std::vector<cudaEvent_t> evs(3 * n_chunks + 1, nullptr);
   struct EvGuard {
-    cudaEvent_t a, b, c, d;
-    ~EvGuard() { for (cudaEvent_t e : {a, b, c, d}) if (e) cudaEventDestroy(e); }
-  } eg{e0, e1, e2, e3};
-  if ((rc = ctr.alloc(6 * sizeof(unsigned long long), s))) return fail(rc);
-  unsigned long long hctr[6];
+    std::vector<cudaEvent_t> &v;
+    ~EvGuard() { for (cudaEvent_t e : v) if (e) cudaEventDestroy(e); }
+  } eg{evs};
+  for (auto &e : evs)
+    if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return fail(MC_ECUDA); }
+  cudaEvent_t e_end = evs.back();
+  if ((rc = ctr.alloc(kCounters * sizeof(unsigned long long), s))) return fail(rc);
+  unsigned long long hctr[kCounters];
   const size_t qb = escape_rec_bytes(ts.precision);
   for (int attempt = 0; attempt < 3; ++attempt) {
     if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
     if ((rc = esc.alloc(cap_q * qb, s))) return fail(rc);
-    if (cudaMemsetAsync(ctr.p, 0, 6 * sizeof(unsigned long long), s) != cudaSuccess) {
+    if (cudaMemsetAsync(ctr.p, 0, kCounters * sizeof(unsigned long long), s) != cudaSuccess) {
       set_error("cudaMemsetAsync failed");
       return fail(MC_ECUDA);
     }
@@ -274,44 +291,59 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     ts.esc_capacity = cap_q;
     ts.esc_cursor = ctr.as<unsigned long long>() + 5;
     ts.records = nullptr;
-    ts.ev_mid = e3;
-    cudaEventRecord(e0, s);
-    if ((rc = run_transport(ts, s))) return fail(rc);
-    cudaEventRecord(e1, s);
+    for (uint64_t c = 0; c < n_chunks; ++c) {
+      ts.first = first + c * kChunk;
+      ts.count = (c + 1 < n_chunks) ? kChunk : count - c * kChunk;
+      ts.ev_mid = evs[3 * c + 1];
+      cudaEventRecord(evs[3 * c], s);
+      if ((rc = run_transport(ts, s))) return fail(rc);
+      cudaEventRecord(evs[3 * c + 2], s);
+      // remember the largest queue fill, empty the queue for the next chunk
+      count_launch();
+      queue_reset_kernel<<<1, 1, 0, s>>>(ctr.as<unsigned long long>());
+      if (cudaGetLastError() != cudaSuccess) { set_error("queue reset launch failed"); return fail(MC_ECUDA); }
+    }
     if (cudaMemcpyAsync(hctr, ctr.p, sizeof(hctr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("transport failed: %s", cudaGetErrorString(cudaGetLastError()));
       return fail(MC_ECUDA);
     }
-    if (hctr[0] <= cap && hctr[5] <= cap_q) break;
+    if (hctr[0] <= cap && hctr[6] <= cap_q) break;
     if (hctr[0] >= 0xFFFFFFFFull) {
       set_error("%llu events exceed the 2^32 limit of one build; split the history range", hctr[0]);
       return fail(MC_EINVAL);
     }
     // rerun with room for everything counted (a lost queue entry also lost
     // its detections, so the event count can grow once more)
-    if (hctr[5] > cap_q) cap_q = hctr[5];
+    if (hctr[6] > cap_q) cap_q = hctr[6];
     if (hctr[0] > cap) cap = hctr[0] + hctr[0] / 8;
     if (attempt == 2) {
       set_error("transport buffers kept overflowing");
       return fail(MC_ECUDA);
     }
   }
+  float t_tr = 0.f, t_det = 0.f;
+  for (uint64_t c = 0; c < n_chunks; ++c) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, evs[3 * c], evs[3 * c + 1]);
+    cudaEventElapsedTime(&b, evs[3 * c + 1], evs[3 * c + 2]);
+    t_tr += a;
+    t_det += b;
+  }
+  cudaEventRecord(evs[0], s);  // reused as the assembly start
   esc.release();
   sys->n_events = (int64_t)hctr[0];
   for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
   rc = assemble_system(sys, events, sys->n_events, s);
   if (rc) return fail(rc);
   if ((rc = finish_system(sys, s))) return fail(rc);
-  cudaEventRecord(e2, s);
-  cudaEventSynchronize(e2);
-  float t1 = 0.f, t2 = 0.f, t3 = 0.f;
-  cudaEventElapsedTime(&t1, e0, e3);
-  cudaEventElapsedTime(&t3, e3, e1);
-  cudaEventElapsedTime(&t2, e1, e2);
-  sys->ms_transport = t1;
-  sys->ms_detect = t3;
-  sys->ms_assembly = t2;
+  cudaEventRecord(e_end, s);
+  cudaEventSynchronize(e_end);
+  float t_asm = 0.f;
+  cudaEventElapsedTime(&t_asm, evs[0], e_end);
+  sys->ms_transport = t_tr;
+  sys->ms_detect = t_det;
+  sys->ms_assembly = t_asm;
   *out = sys;
   return MC_OK;
 }

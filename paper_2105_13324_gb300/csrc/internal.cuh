@@ -111,6 +111,11 @@ struct mc_system {
   mcs::DevBuf ll;       // f64 [ll_cap]
   int64_t ll_cap = 0;
   int spmv_group_fwd = 4, spmv_group_bwd = 4;  // lanes per row / per column
+  // tile partition of the non-zeros for the streaming SpMV kernels (empty:
+  // fall back to the row-group kernels)
+  mcs::DevBuf csr_blocks, csc_blocks;  // u32 [n_blocks + 1] first row / column of each tile
+  int64_t n_csr_blocks = 0, n_csc_blocks = 0;
+  bool warp_rows_fwd = false, warp_rows_bwd = false;
 };
 
 namespace mcs {
@@ -166,6 +171,9 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s);
 
 // Projector value arrays for sys->value_type.
 int make_values(mc_system *sys, cudaStream_t s);
+
+// Tile partition of CSR and CSC for the streaming SpMV kernels (mlem.cu).
+int make_stream_blocks(mc_system *sys, cudaStream_t s);
 
 // Scans / sorts (assemble.cu)
 int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);

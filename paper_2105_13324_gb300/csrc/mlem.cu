@@ -45,6 +45,66 @@ __device__ __forceinline__ double block_sum_double(double v, double *s_tmp) {
   return t;
 }
 
+// Partial sum, for lane `sub` of a group of G lanes, of val[k] * vec[idx[k]]
+// over k in [b, e).  The matrix streams are read with 16-byte vector loads
+// (4 entries per lane per step) between a scalar head that reaches a
+// multiple of 4 and a scalar tail, and with the streaming cache hint so that
+// they do not evict the gathered vector from L2.
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+  const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const __half *p, float v[4]) {
+  const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16 *p, float v[4]) {
+  const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename V, int G>
+__device__ __forceinline__ float segment_dot(uint32_t b, uint32_t e, const uint32_t *__restrict__ idx,
+                                             const V *__restrict__ val, const float *__restrict__ vec, int sub) {
+  float acc = 0.0f;
+  uint32_t a = (b + 3u) & ~3u;
+  if (a > e) a = e;
+  for (uint32_t k = b + sub; k < a; k += G) acc = fmaf(to_f(__ldcs(val + k)), __ldg(vec + __ldcs(idx + k)), acc);
+  const uint32_t t = a + ((e - a) & ~3u);
+  uint32_t k = a + 4u * sub;
+  // two 4-entry vectors per lane per step: both loads issue before the gathers
+  for (; k + 4u * G < t; k += 8u * G) {
+    const uint4 i4 = __ldcs(reinterpret_cast<const uint4 *>(idx + k));
+    const uint4 j4 = __ldcs(reinterpret_cast<const uint4 *>(idx + k + 4u * G));
+    float v[4], w[4];
+    load4(val + k, v);
+    load4(val + k + 4u * G, w);
+    acc = fmaf(v[0], __ldg(vec + i4.x), acc);
+    acc = fmaf(v[1], __ldg(vec + i4.y), acc);
+    acc = fmaf(v[2], __ldg(vec + i4.z), acc);
+    acc = fmaf(v[3], __ldg(vec + i4.w), acc);
+    acc = fmaf(w[0], __ldg(vec + j4.x), acc);
+    acc = fmaf(w[1], __ldg(vec + j4.y), acc);
+    acc = fmaf(w[2], __ldg(vec + j4.z), acc);
+    acc = fmaf(w[3], __ldg(vec + j4.w), acc);
+  }
+  for (; k < t; k += 4u * G) {
+    const uint4 i4 = __ldcs(reinterpret_cast<const uint4 *>(idx + k));
+    float v[4];
+    load4(val + k, v);
+    acc = fmaf(v[0], __ldg(vec + i4.x), acc);
+    acc = fmaf(v[1], __ldg(vec + i4.y), acc);
+    acc = fmaf(v[2], __ldg(vec + i4.z), acc);
+    acc = fmaf(v[3], __ldg(vec + i4.w), acc);
+  }
+  for (uint32_t k = t + sub; k < e; k += G) acc = fmaf(to_f(__ldcs(val + k)), __ldg(vec + __ldcs(idx + k)), acc);
+  return acc;
+}
+
 // MODE 0: out = q.  MODE 1: out = r = y / q (0 where q = 0), and with LL the
 // block's share of sum_j (y_j ln q_j - q_j) in partials[blockIdx.x].
 template <typename V, int G, int MODE, bool LL>
@@ -62,8 +122,7 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
   // empty range
   uint32_t b = 0, e = 0;
   if (gid < m) { b = row_ptr[gid]; e = row_ptr[gid + 1]; }
-  float acc = 0.0f;
-  for (uint32_t k = b + sub; k < e; k += G) acc = fmaf(to_f(val[k]), __ldg(xs + col[k]), acc);
+  float acc = segment_dot<V, G>(b, e, col, val, xs, sub);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
   if (gid < m && sub == 0) {
@@ -95,8 +154,7 @@ __global__ void __launch_bounds__(kSpmvThreads) csc_back_kernel(const uint32_t *
   const int sub = threadIdx.x & (G - 1);
   uint32_t b = 0, e = 0;
   if (gid < n) { b = col_ptr[gid]; e = col_ptr[gid + 1]; }
-  float acc = 0.0f;
-  for (uint32_t k = b + sub; k < e; k += G) acc = fmaf(to_f(val[k]), __ldg(r + row[k]), acc);
+  float acc = segment_dot<V, G>(b, e, row, val, r, sub);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
   if (gid < n && sub == 0) {
@@ -159,6 +217,141 @@ __global__ void sensitivity_kernel(const double *colsum, const uint32_t *n_v, in
 }
 
 // ---------------------------------------------------------------------------
+// streaming SpMV: one block per tile of at most kStreamTile non-zeros
+// ---------------------------------------------------------------------------
+// A tile is a run of whole rows (columns) whose entries are contiguous in the
+// CSR (CSC) arrays.  The block first reads the tile's entries and gathers the
+// vector with independent, coalesced loads (many requests in flight), keeps
+// the products in shared memory, and then reduces each row from shared
+// memory: one thread per row for short rows, one warp per row for long ones.
+// Every row is summed in a fixed order, so results are reproducible.
+constexpr int kStreamTile = 4096;
+constexpr int kStreamThreads = 256;
+
+template <typename V>
+__device__ __forceinline__ void stream_products(uint32_t p0, uint32_t cnt, const uint32_t *__restrict__ idx,
+                                                const V *__restrict__ val, const float *__restrict__ vec,
+                                                float *s_prod) {
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < cnt; i += kStreamThreads) {
+    const uint32_t k = p0 + i;
+    s_prod[i] = to_f(__ldcs(val + k)) * __ldg(vec + __ldcs(idx + k));
+  }
+}
+
+// Sum of the products of segment [b, e) of the tile: one thread, or the 32
+// lanes of a warp (result in every lane).
+template <bool WARP>
+__device__ __forceinline__ float stream_segment(const float *s_prod, uint32_t b, uint32_t e) {
+  float acc = 0.0f;
+  if (WARP) {
+    for (uint32_t k = b + (threadIdx.x & 31); k < e; k += 32) acc += s_prod[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  } else {
+    for (uint32_t k = b; k < e; ++k) acc += s_prod[k];
+  }
+  return acc;
+}
+
+template <typename V, bool WARP, int MODE, bool LL>
+__global__ void __launch_bounds__(kStreamThreads) stream_forward_kernel(const uint32_t *__restrict__ row_ptr,
+                                                                     const uint32_t *__restrict__ tiles,
+                                                                     const uint32_t *__restrict__ col,
+                                                                     const V *__restrict__ val,
+                                                                     const float *__restrict__ xs,
+                                                                     const float *__restrict__ y,
+                                                                     float *__restrict__ out, double *partials) {
+  __shared__ float s_prod[kStreamTile];
+  __shared__ double s_tmp[kStreamThreads / 32];
+  const uint32_t r0 = tiles[blockIdx.x], r1 = tiles[blockIdx.x + 1];
+  const uint32_t p0 = row_ptr[r0];
+  stream_products<V>(p0, row_ptr[r1] - p0, col, val, xs, s_prod);
+  __syncthreads();
+  double ll = 0.0;
+  const uint32_t first = WARP ? (threadIdx.x >> 5) : threadIdx.x;
+  const uint32_t step = WARP ? kStreamThreads / 32 : kStreamThreads;
+  for (uint32_t r = r0 + first; r < r1; r += step) {
+    const float acc = stream_segment<WARP>(s_prod, row_ptr[r] - p0, row_ptr[r + 1] - p0);
+    if (!WARP || (threadIdx.x & 31) == 0) {
+      if (MODE == 0) {
+        out[r] = acc;
+      } else {
+        const float yj = y[r];
+        out[r] = acc > 0.0f ? yj / acc : 0.0f;
+        if (LL) ll += (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+      }
+    }
+  }
+  if (LL) {
+    const double t = block_sum_double(ll, s_tmp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+template <typename V, bool WARP, int MODE>
+__global__ void __launch_bounds__(kStreamThreads) stream_back_kernel(const uint32_t *__restrict__ col_ptr,
+                                                                  const uint32_t *__restrict__ tiles,
+                                                                  const uint32_t *__restrict__ row,
+                                                                  const V *__restrict__ val,
+                                                                  const float *__restrict__ r,
+                                                                  const float *__restrict__ inv_n,
+                                                                  const float *__restrict__ inv_colsum,
+                                                                  float *__restrict__ x, float *__restrict__ xs) {
+  __shared__ float s_prod[kStreamTile];
+  const uint32_t c0 = tiles[blockIdx.x], c1 = tiles[blockIdx.x + 1];
+  const uint32_t p0 = col_ptr[c0];
+  stream_products<V>(p0, col_ptr[c1] - p0, row, val, r, s_prod);
+  __syncthreads();
+  const uint32_t first = WARP ? (threadIdx.x >> 5) : threadIdx.x;
+  const uint32_t step = WARP ? kStreamThreads / 32 : kStreamThreads;
+  for (uint32_t v = c0 + first; v < c1; v += step) {
+    const float acc = stream_segment<WARP>(s_prod, col_ptr[v] - p0, col_ptr[v + 1] - p0);
+    if (!WARP || (threadIdx.x & 31) == 0) {
+      if (MODE == 0) {
+        x[v] = acc * inv_n[v];
+      } else {
+        const float is = inv_colsum[v];
+        const float xn = is > 0.0f ? x[v] * acc * is : 0.0f;
+        x[v] = xn;
+        xs[v] = xn * inv_n[v];
+      }
+    }
+  }
+}
+
+// longest segment of a CSR/CSC pointer array
+__global__ void max_segment_kernel(const uint32_t *ptr, int64_t n, unsigned int *out) {
+  uint32_t mx = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t len = ptr[i + 1] - ptr[i];
+    mx = len > mx ? len : mx;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t y2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y2 > mx ? y2 : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+// tiles[b] = first segment whose start is >= b * step (tiles[n_tiles] = n).
+// With step = kStreamTile - longest segment, each tile holds fewer than
+// kStreamTile entries.
+__global__ void tile_bounds_kernel(const uint32_t *ptr, int64_t n, uint32_t step, int64_t n_tiles, uint32_t *tiles) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= n_tiles; b += (int64_t)gridDim.x * blockDim.x) {
+    if (b == n_tiles) { tiles[b] = (uint32_t)n; continue; }
+    const uint64_t target = (uint64_t)b * step;
+    int64_t lo = 0, hi = n;  // first i in [0, n] with ptr[i] >= target
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((uint64_t)ptr[mid] >= target) hi = mid; else lo = mid + 1;
+    }
+    tiles[b] = (uint32_t)lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
 static int grid_stride_blocks(int64_t n) {
@@ -202,9 +395,41 @@ static void back_launch(const mc_system *sys, int g, const float *r, float *x, f
   }
 }
 
+template <typename V, int MODE, bool LL>
+static void stream_fwd_launch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
+                              cudaStream_t s) {
+  const unsigned nb = (unsigned)sys->n_csr_blocks;
+  const uint32_t *rp = sys->row_ptr.as<uint32_t>(), *t = sys->csr_blocks.as<uint32_t>(), *ci = sys->col_idx.as<uint32_t>();
+  const V *val = sys->csr_val.as<V>();
+  count_launch();
+  if (sys->warp_rows_fwd)
+    stream_forward_kernel<V, true, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials);
+  else
+    stream_forward_kernel<V, false, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials);
+}
+
+template <typename V, int MODE>
+static void stream_back_launch(const mc_system *sys, const float *r, float *x, float *xs, cudaStream_t s) {
+  const unsigned nb = (unsigned)sys->n_csc_blocks;
+  const uint32_t *cp = sys->col_ptr.as<uint32_t>(), *t = sys->csc_blocks.as<uint32_t>(), *ri = sys->row_idx.as<uint32_t>();
+  const V *val = sys->csc_val.as<V>();
+  const float *inv_n = sys->inv_n.as<float>(), *ics = sys->inv_colsum.as<float>();
+  count_launch();
+  if (sys->warp_rows_bwd)
+    stream_back_kernel<V, true, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
+  else
+    stream_back_kernel<V, false, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
+}
+
 template <int MODE, bool LL>
 static void fwd_dispatch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
                          cudaStream_t s) {
+  if (sys->n_csr_blocks > 0) {
+    if (sys->value_type == MC_VAL_F16) stream_fwd_launch<__half, MODE, LL>(sys, xs, y, out, partials, s);
+    else if (sys->value_type == MC_VAL_BF16) stream_fwd_launch<__nv_bfloat16, MODE, LL>(sys, xs, y, out, partials, s);
+    else stream_fwd_launch<float, MODE, LL>(sys, xs, y, out, partials, s);
+    return;
+  }
   const int g = sys->spmv_group_fwd;
   if (sys->value_type == MC_VAL_F16) fwd_launch<__half, MODE, LL>(sys, g, xs, y, out, partials, s);
   else if (sys->value_type == MC_VAL_BF16) fwd_launch<__nv_bfloat16, MODE, LL>(sys, g, xs, y, out, partials, s);
@@ -213,13 +438,56 @@ static void fwd_dispatch(const mc_system *sys, const float *xs, const float *y, 
 
 template <int MODE>
 static void back_dispatch(const mc_system *sys, const float *r, float *x, float *xs, cudaStream_t s) {
+  if (sys->n_csc_blocks > 0) {
+    if (sys->value_type == MC_VAL_F16) stream_back_launch<__half, MODE>(sys, r, x, xs, s);
+    else if (sys->value_type == MC_VAL_BF16) stream_back_launch<__nv_bfloat16, MODE>(sys, r, x, xs, s);
+    else stream_back_launch<float, MODE>(sys, r, x, xs, s);
+    return;
+  }
   const int g = sys->spmv_group_bwd;
   if (sys->value_type == MC_VAL_F16) back_launch<__half, MODE>(sys, g, r, x, xs, s);
   else if (sys->value_type == MC_VAL_BF16) back_launch<__nv_bfloat16, MODE>(sys, g, r, x, xs, s);
   else back_launch<float, MODE>(sys, g, r, x, xs, s);
 }
 
-int forward_blocks(const mc_system *sys) { return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads); }
+int forward_blocks(const mc_system *sys) {
+  if (sys->n_csr_blocks > 0) return (int)sys->n_csr_blocks;
+  return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads);
+}
+
+// Tiles for one pointer array: none (row-group kernels) when a segment is
+// longer than half a tile.
+static int stream_tiles(const DevBuf &ptr, int64_t n, int64_t nnz, DevBuf &tiles, int64_t &n_tiles, bool &warp,
+                        cudaStream_t s) {
+  n_tiles = 0;
+  if (n <= 0 || nnz <= 0) return MC_OK;
+  DevBuf mx;
+  MCS_TRY(mx.alloc(sizeof(unsigned int), s));
+  MCS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), s));
+  count_launch();
+  max_segment_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(ptr.as<uint32_t>(), n, mx.as<unsigned int>());
+  MCS_LAUNCHED();
+  unsigned int longest = 0;
+  MCS_CUDA(cudaMemcpyAsync(&longest, mx.p, sizeof(longest), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  // tiles pay off for short segments; long ones stream better per row group
+  if ((int64_t)longest * 2 > kStreamTile || (double)nnz / (double)n >= 32.0) return MC_OK;
+  const uint32_t step = (uint32_t)(kStreamTile - longest);
+  n_tiles = (nnz + step - 1) / step;
+  MCS_TRY(tiles.alloc((size_t)(n_tiles + 1) * sizeof(uint32_t), s));
+  count_launch();
+  tile_bounds_kernel<<<grid_stride_blocks(n_tiles + 1), 256, 0, s>>>(ptr.as<uint32_t>(), n, step, n_tiles,
+                                                                     tiles.as<uint32_t>());
+  MCS_LAUNCHED();
+  warp = (double)nnz / (double)n >= 16.0;
+  return MC_OK;
+}
+
+int make_stream_blocks(mc_system *sys, cudaStream_t s) {
+  MCS_TRY(stream_tiles(sys->row_ptr, sys->n_rows, sys->nnz, sys->csr_blocks, sys->n_csr_blocks, sys->warp_rows_fwd, s));
+  MCS_TRY(stream_tiles(sys->col_ptr, sys->n_cols, sys->nnz, sys->csc_blocks, sys->n_csc_blocks, sys->warp_rows_bwd, s));
+  return MC_OK;
+}
 
 int project(const mc_system *sys, const float *x, float *q, cudaStream_t s) {
   if (sys->n_cols > 0) {
