@@ -138,6 +138,12 @@ def shard_seed(base_seed: int, rank: int) -> int:
     return base_seed + 7919 * rank
 
 
+def whole_job_rate(world_size: int, histories_per_rank: int, max_ms_per_step: float) -> float:
+    """Histories per second of the whole job: every rank runs its own
+    histories, the slowest rank sets the step time."""
+    return world_size * histories_per_rank / (max_ms_per_step * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle arm (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -209,6 +215,64 @@ def run_reference(args, w):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def spmv_bytes(system, nnz, M, N, val_bytes):
+    """Algorithmic bytes of one ML-EM iteration: both matrix streams, the
+    pointer arrays, and the vectors over non-empty rows / columns (x gathered
+    once, y, r written and read, s, x read and written)."""
+    rp, _, _ = system.export_csr()
+    cp, _, _, _ = system.export_csc()
+    m_nz = int(np.count_nonzero(np.diff(rp)))
+    n_nz = int(np.count_nonzero(np.diff(cp)))
+    return (2 * nnz * (val_bytes + 4) + 4 * (M + 1) + 4 * (N + 1)
+            + 4 * (n_nz + m_nz + 2 * m_nz + n_nz + 2 * n_nz))
+
+
+def mlem_timing(mc, system, y, x, n_iter, flush, stream, reps=5, label="f32"):
+    """Median device time of n_iter ML-EM iterations (L2 flushed before each
+    repetition), CUDA events on the launching stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        mc.mc_mlem_init(system, y, x)
+        e0.record(stream)
+        mc.mlem_iterate(system, y, x, n_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    it = float(np.median(ms)) / n_iter
+    return {label: {"ms_per_iter": it, "iter_per_s": 1e3 / it}}
+
+
+def roof_instance(mc, plan, histories, seed, n_iter, flush, stream, hbm_gbs, peak_kind):
+    """Build the benchmark geometry with `histories` histories (a matrix far
+    larger than L2) and time the SpMV pair against HBM bandwidth."""
+    import torch
+    s = plan.build(0, histories, seed + 2000)
+    inf = s.info()
+    M, N = inf["n_rows"], inf["n_cols"]
+    y = torch.rand(M, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7)) * 10.0
+    x = torch.ones(N, device="cuda")
+    out = {"histories": histories, "nnz": inf["nnz"], "build_s": (inf["build_ms_transport"] + inf["build_ms_detect"]
+                                                                  + inf["build_ms_assembly"]) / 1e3}
+    reps_iter = min(n_iter, 20)
+    for vt, vb in (("f32", 4), ("f16", 2)):
+        if vt == "f16" and inf["max_count"] > 2048:
+            continue
+        s.set_value_type(vt)
+        mc.mc_mlem_init(s, y, x)
+        mc.mlem_iterate(s, y, x, 3)
+        t = mlem_timing(mc, s, y, x, reps_iter, flush, stream, reps=3, label=vt)[vt]
+        b = spmv_bytes(s, inf["nnz"], M, N, vb)
+        gbs = b / (t["ms_per_iter"] * 1e-3) / 1e9
+        out[vt] = {"ms_per_iter": t["ms_per_iter"], "bytes_per_iter": b, "achieved_gbs": gbs, "frac": gbs / hbm_gbs}
+    out["peak_gbs"] = hbm_gbs
+    out["peak_kind"] = peak_kind
+    s.free()
+    return out
+
+
 def run_ours(args, w):
     import torch
 
@@ -278,30 +342,39 @@ def run_ours(args, w):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = _maxreduce(float(np.mean(step_ms)), ws, dev)
-    value = ws * H / (ms * 1e-3)
+    value = whole_job_rate(ws, H, ms)
 
-    # ML-EM alone on the last system: iterations/s and the SpMV roofline
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    mlem_ms = []
-    for _ in range(reps):
-        flush.zero_()
-        mc.mc_mlem_init(last, y, x)
-        e0.record(stream)
-        mc.mlem_iterate(last, y, x, n_iter)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mlem_ms.append(e0.elapsed_time(e1))
-    it_ms = float(np.median(mlem_ms)) / n_iter
+    # ML-EM alone on the last system: iterations/s per value type
     inf = infos[-1]
-    nnz = inf["nnz"]
-    rp, _, _ = last.export_csr()
-    cp, _, _, _ = last.export_csc()
-    m_nz = int(np.count_nonzero(np.diff(rp)))
-    n_nz = int(np.count_nonzero(np.diff(cp)))
-    mlem_bytes = (2 * nnz * (4 + 4) + 4 * (M + 1) + 4 * (N + 1)
-                  + 4 * (n_nz + m_nz + 2 * m_nz + n_nz + 2 * n_nz))
     hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+    mlem = mlem_timing(mc, last, y, x, n_iter, flush, stream)
+    it_ms = mlem["f32"]["ms_per_iter"]
+    value_types = {}
+    x32 = None
+    for vt in ("f32", "f16", "bf16"):
+        if vt != "f32":
+            limit = 2048 if vt == "f16" else 256
+            if inf["max_count"] > limit:
+                value_types[vt] = {"skipped": f"counts up to {inf['max_count']} not exact"}
+                continue
+            last.set_value_type(vt)
+            t = mlem_timing(mc, last, y, x, n_iter, flush, stream, label=vt)[vt]
+        else:
+            t = mlem[vt]
+        mc.mc_mlem_init(last, y, x)
+        mc.mlem_iterate(last, y, x, n_iter)
+        img = x.cpu().numpy().astype(np.float64)
+        if vt == "f32":
+            x32 = img
+        t["rel_l2_vs_f32"] = float(np.linalg.norm(img - x32) / max(np.linalg.norm(x32), 1e-300))
+        value_types[vt] = t
+    last.set_value_type("f32")
+    mlem_bytes = spmv_bytes(last, inf["nnz"], M, N, 4)
+
+    # SpMV roofline on a matrix larger than L2 (same geometry, more histories)
+    roof = None
+    if args.roof_histories and rank == 0:
+        roof = roof_instance(mc, plan, int(args.roof_histories), seed, n_iter, flush, stream, hbm_gbs, peak_kind)
 
     # transport roofline (lane-op issue bound), work counted from an FP64
     # trace of a history sample of this workload
@@ -338,7 +411,7 @@ def run_ours(args, w):
         t0 = time.perf_counter()
         e2e_step()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_val = ws * H / (_maxreduce(float(np.mean(e2e_ms)), ws, dev) * 1e-3)
+    e2e_val = whole_job_rate(ws, H, _maxreduce(float(np.mean(e2e_ms)), ws, dev))
     n_mat = len(w.phantom.rho)
     V = w.geometry.n_views
     h2d = w.phantom.material.size + 3 * 8 * n_mat + 2 * V * (8 + 4) + 3 * n_mat * (8 + 4) + 4 * M
@@ -371,7 +444,9 @@ def run_ours(args, w):
             "roofline_mlem": {"bound": "hbm", "achieved": mlem_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm_gbs,
                               "unit": "GB/s", "frac": mlem_bytes / (it_ms * 1e-3) / 1e9 / hbm_gbs,
                               "traffic": None, "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
-                              "note": "matrix of this workload fits in L2"},
+                              "note": "benchmark matrix (largely L2-resident)"},
+            "roofline_mlem_roof": roof,
+            "mlem_value_types": value_types,
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -398,6 +473,8 @@ def main(argv=None):
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roof-histories", type=float, default=1e11,
+                    help="histories of the large-matrix SpMV roofline instance (0: skip)")
     args = ap.parse_args(argv)
     w = P.workload(args.workload)
     if args.impl == "reference":
