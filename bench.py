@@ -322,7 +322,7 @@ def run_ours(args, w):
     _barrier(ws)
     torch.cuda.synchronize()
     l0 = mc.mc_kernel_launches()
-    t_transport, t_assembly, infos = [], [], []
+    t_transport, t_detect, t_assembly, infos = [], [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -330,6 +330,7 @@ def run_ours(args, w):
         ev[k][1].record(stream)
         inf = s.info()
         t_transport.append(inf["build_ms_transport"])
+        t_detect.append(inf["build_ms_detect"])
         t_assembly.append(inf["build_ms_assembly"])
         infos.append(inf)
         if k == args.steps - 1:
@@ -433,9 +434,10 @@ def run_ours(args, w):
                        "parallelism": f"{ws} independent acquisitions" if ws > 1 else "1 GPU"},
             "mlem_iter_per_s": 1e3 / it_ms,
             "transport_histories_per_s": H / (t_tr * 1e-3),
-            "step_breakdown_ms": {"transport": t_tr, "assembly": float(np.mean(t_assembly)),
+            "step_breakdown_ms": {"transport": t_tr, "detect": float(np.mean(t_detect)),
+                                  "assembly": float(np.mean(t_assembly)),
                                   "mlem": it_ms * n_iter},
-            "matrix": {"rows": M, "cols": N, "nnz": nnz, "events": inf["n_events"], "fates": inf["fates"],
+            "matrix": {"rows": M, "cols": N, "nnz": inf["nnz"], "events": inf["n_events"], "fates": inf["fates"],
                        "max_count": inf["max_count"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                          "frac": achieved / alu_peak, "traffic": None, "kernel": "transport_kernel<float>",
