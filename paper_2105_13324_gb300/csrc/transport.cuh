@@ -39,6 +39,8 @@ constexpr double kMec2 = 510.99895;       // electron rest energy, keV
 constexpr double kRe = 2.8179403262e-13;  // classical electron radius, cm
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSigTab = 256;              // float path: sigma_KN table over [E_low, E0]
+constexpr int kWaitCollide = 16;          // lanes waiting at a real collision before a warp handles them
+constexpr int kWaitEmit = 8;             // lanes waiting for a new history before a warp emits
 
 template <typename T> struct TArgs {
   const uint8_t *mat;
@@ -54,6 +56,7 @@ template <typename T> struct TArgs {
   T w_max;           // |d_z| bound above which no view can accept (with margin)
   T start_deg, inv_delta, psi_views;  // azimuth window of candidate views
   int views_per_turn;                 // 360 / delta if integral, else 0
+  int t_coll, t_emit;                 // lanes that must wait before a warp runs collisions / emissions
   T sigma, plane, bin, half_bu, half_bv;
   int n_views, bins_u, bins_v;
   uint32_t n_vox;
@@ -459,17 +462,66 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
   en0.set(a.e0, a, s_sig);
   uint32_t steps = 0, n_virtual = 0, n_real = 0, n_compton = 0;
   uint64_t cur_i = 0;
-  bool alive = false;
   uint32_t n_fate[4] = {0u, 0u, 0u, 0u};  // fates of this thread's histories
 
   RingRng<TArgs<T>> rng{rg, a};
+  // Lane states.  A lane that reaches a real collision, or needs a new
+  // history, waits until at least t_coll (t_emit) lanes of its warp wait for
+  // the same step -- or no lane is left flying -- so that the long collision
+  // and emission steps run with many lanes at once while the others keep
+  // flying.  All 32 lanes run every iteration (warp-uniform loop).
+  enum { S_FLY = 0, S_COLLIDE = 1, S_EMIT = 2, S_DONE = 3 };
+  int st = (i < a.count) ? S_EMIT : S_DONE;
+  int m_col = 0;      // material at the pending real collision
+  T mu_col = (T)0;    // and its attenuation
   for (;;) {
-    if (!alive && i >= a.count) break;
+    const unsigned m_emit = __ballot_sync(0xffffffffu, st == S_EMIT);
+    const unsigned m_coll = __ballot_sync(0xffffffffu, st == S_COLLIDE);
+    const unsigned m_fly = __ballot_sync(0xffffffffu, st == S_FLY);
+    if ((m_emit | m_coll | m_fly) == 0u) break;
+    const bool do_coll = m_coll != 0u && (__popc(m_coll) >= a.t_coll || m_fly == 0u);
+    const bool do_emit = m_emit != 0u && (__popc(m_emit) >= a.t_emit || m_fly == 0u);
+    {
+      // the one Philox point: words for everything this lane does below
+      // (emission 5 + flight 2; collision: photo 1 + three rejection trials
+      // 6 + azimuth 1 + flight 2; flight 2); a scatter needing more trials
+      // draws the rest inline
+      uint32_t need = 0u;
+      if (st == S_FLY) need = 2u;
+      else if (st == S_EMIT && do_emit) need = 7u;
+      else if (st == S_COLLIDE && do_coll) need = 10u;
+      while (rg.avail < need) rg.refill(a);
+    }
     int fate = -1;
-    if (!alive) {
+    if (do_coll && st == S_COLLIDE) {
+      // photo-absorption, else a Klein-Nishina scatter, at the pending collision
+      rg.ensure(1, a);
+      if (uniform<T>(rg.next()) * mu_col < mu_photo<T>(s_c0, s_c1, s_c2, m_col, en)) {
+        fate = MC_FATE_ABSORBED;
+      } else {
+        T mu_c, eps;
+        if (!compton<T>(rng, en.e, mu_c, eps)) {
+          fate = MC_FATE_CAP;
+        } else {
+          rg.ensure(1, a);
+          T cp, sp;
+          cos_sin_2pi<T>(uniform<T>(rg.next()), cp, sp);
+          rotate<T>(dx, dy, dz, mu_c, cp, sp);
+          const T e_new = eps * en.e;
+          n_compton += 1;
+          if (e_new < a.e_low) {
+            en.e = e_new;
+            fate = MC_FATE_BELOW_WINDOW;
+          } else {
+            en.set(e_new, a, s_sig);
+            st = S_FLY;
+          }
+        }
+      }
+    }
+    if (do_emit && st == S_EMIT) {
       // emission (Sec. 3, isotropic 4 pi): uniform point in voxel v, uniform
       // direction; five draws
-      rg.ensure(4, a);
       cur_i = i;
       px = ((T)vi + uniform<T>(rg.next())) * a.h - a.hx;
       py = ((T)vj + uniform<T>(rg.next())) * a.h - a.hy;
@@ -482,7 +534,6 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       vk += sk;
       if (vk >= nz) vk -= nz;
       const T ct = (T)2 * uniform<T>(rg.next()) - (T)1;
-      rg.ensure(1, a);
       T cph, sph;
       cos_sin_2pi<T>(uniform<T>(rg.next()), cph, sph);
       const T sth = sqrt0<T>((T)1 - ct * ct);
@@ -491,16 +542,16 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       dz = ct;
       en = en0;
       steps = n_virtual = n_real = n_compton = 0;
-      alive = true;
+      st = S_FLY;
       if (!(a.mu_maj > (T)0)) fate = MC_FATE_ESCAPE;
     }
-    if (fate < 0) {
+    if (st == S_FLY && fate < 0) {
       // one Woodcock flight over the majorant
       if (steps >= kStepCap) {
         fate = MC_FATE_CAP;
       } else {
         steps += 1;
-        rg.ensure(2, a);  // the flight and its real/virtual test
+        rg.ensure(2, a);
         const T s = flight<T>(uniform<T>(rg.next()), a);
         const T qx = px + s * dx, qy = py + s * dy, qz = pz + s * dz;
         if (!(qx >= -a.hx && qx < a.hx && qy >= -a.hy && qy < a.hy && qz >= -a.hz && qz < a.hz)) {
@@ -514,28 +565,9 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
           const T mu = mu_total<T>(s_c0, s_c1, s_c2, m, en);
           if (uniform<T>(rg.next()) * a.mu_maj < mu) {
             n_real += 1;
-            rg.ensure(1, a);
-            if (uniform<T>(rg.next()) * mu < mu_photo<T>(s_c0, s_c1, s_c2, m, en)) {
-              fate = MC_FATE_ABSORBED;
-            } else {
-              T mu_c, eps;
-              if (!compton<T>(rng, en.e, mu_c, eps)) {
-                fate = MC_FATE_CAP;
-              } else {
-                rg.ensure(1, a);
-                T cp, sp;
-                cos_sin_2pi<T>(uniform<T>(rg.next()), cp, sp);
-                rotate<T>(dx, dy, dz, mu_c, cp, sp);
-                const T e_new = eps * en.e;
-                n_compton += 1;
-                if (e_new < a.e_low) {
-                  en.e = e_new;
-                  fate = MC_FATE_BELOW_WINDOW;
-                } else {
-                  en.set(e_new, a, s_sig);
-                }
-              }
-            }
+            m_col = m;
+            mu_col = mu;
+            st = S_COLLIDE;
           } else {
             n_virtual += 1;
           }
@@ -578,8 +610,12 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
         for (int e = 0; e < 4; ++e) rec.event_row[e] = 0;
         a.records[cur_i] = rec;
       }
-      alive = false;
-      rg.start(a.first + i);  // next history's stream (unused past the end)
+      if (i < a.count) {
+        st = S_EMIT;
+        rg.start(a.first + i);  // next history's stream
+      } else {
+        st = S_DONE;
+      }
     }
   }
   // fates: warp sums, then one shared atomic per warp and fate
@@ -797,6 +833,8 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.first = ts.first; a.count = ts.count;
   a.events = ts.events; a.capacity = ts.capacity; a.cursor = ts.cursor; a.fates = ts.fates;
   a.records = ts.records;
+  a.t_coll = kWaitCollide;
+  a.t_emit = kWaitEmit;
   a.esc = ts.esc;
   a.esc_capacity = ts.esc_capacity;
   a.esc_cursor = ts.esc_cursor;
