@@ -49,6 +49,10 @@ extern "C" {
 #define MC_FP32 0 /* production: float arithmetic, 23-bit uniforms */
 #define MC_FP64 1 /* verification: double arithmetic, 32-bit uniforms */
 
+/* what the transport tallies */
+#define MC_TALLY_ALL 0
+#define MC_TALLY_PRIMARY 1
+
 /* storage type of matrix values used by the projectors */
 #define MC_VAL_F32 0
 #define MC_VAL_F16 1
@@ -92,6 +96,9 @@ typedef struct mc_geometry {
   double e0_kev, window_frac;
   double photo_k;
   int32_t precision; /* MC_FP32 or MC_FP64 */
+  int32_t tally;     /* MC_TALLY_ALL, or MC_TALLY_PRIMARY: only photons that
+                        reach the camera unscattered (the attenuation + blur
+                        matrix of dual-matrix OS, Sec. 5.3) */
 } mc_geometry;
 
 typedef struct mc_system mc_system; /* opaque, device resident */
@@ -200,6 +207,30 @@ MC_API int mc_mlem_init(mc_system *sys, const float *y_dev, float *x_dev, void *
  * the iterates before each update, and the call synchronises `stream`. */
 MC_API int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter, double *loglik_host,
                  void *stream);
+
+/* Ordered subsets (Sec. 5.3, OSEM): the system made of the rows of views
+ * subset, subset + n_subsets, subset + 2 n_subsets, ... of a full system
+ * whose rows are view-major with rows_per_view rows per view (n_bins_v *
+ * n_bins_u for systems built here).  Its row i is parent row
+ * (subset + (i / rows_per_view) n_subsets) rows_per_view + i % rows_per_view;
+ * columns, n_v and counts are the parent's.  Errors: MC_EINVAL if the parent
+ * is itself a subset or the sizes do not fit. */
+MC_API int mc_system_subset(const mc_system *parent, int64_t rows_per_view, int32_t n_subsets, int32_t subset,
+                            void *stream, mc_system **out);
+
+/* n_iter sweeps of ordered-subset EM (Sec. 5.3) with the dual-matrix
+ * update of Eq. (DMOS) and the additive term of Eq. (Sohlberg OSEM), in
+ * place on x_dev[N]: for s = 0 .. n_subsets-1,
+ *   q = C_s x,  r_i = y_o / (q_i + add_o) (0 if not positive), o the parent
+ *   row of subset row i,
+ *   x_v <- x_v / sum_i B_s,iv * sum_i B_s,iv r_i   (x_v = 0 where the sum is 0)
+ * with C_s = fwd[s] (reprojection, e.g. all photons) and B_s = back[s]
+ * (back-projection, e.g. MC_TALLY_PRIMARY).  fwd[s] and back[s] must be
+ * subset s of n_subsets (n_subsets = 1: full systems) of the same shape.
+ * y_dev and add_dev (nullable: no additive term) have the parent's rows.
+ * fwd = back with one subset and no additive term is mlem_iterate. */
+MC_API int osem_iterate(mc_system *const *fwd, mc_system *const *back, int32_t n_subsets, const float *y_dev,
+                        const float *add_dev, float *x_dev, int32_t n_iter, void *stream);
 
 /* ML-EM like mlem_iterate, for callers that must not allocate device
  * memory: a reconstruction service that plans its memory up front (a device

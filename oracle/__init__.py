@@ -75,6 +75,7 @@ class _Problem(ctypes.Structure):
         ("hole_len_mm", ctypes.c_double), ("hole_diam_mm", ctypes.c_double),
         ("fwhm_mm", ctypes.c_double), ("e0_kev", ctypes.c_double),
         ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double),
+        ("primary_only", ctypes.c_int32),
     ]
 
 
@@ -114,7 +115,7 @@ class Problem:
     """A phantom + geometry pair marshalled for the C oracle.  Keeps the
     NumPy buffers alive for as long as the struct is in use."""
 
-    def __init__(self, phantom, geometry):
+    def __init__(self, phantom, geometry, primary_only: bool = False):
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -127,7 +128,8 @@ class Problem:
                           self.rho.ctypes.data, self.zoa.ctypes.data, self.zeff.ctypes.data,
                           g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
                           float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
-                          float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k))
+                          float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
+                          int(bool(primary_only)))
 
     @property
     def ref(self):
@@ -314,3 +316,38 @@ def mlem(a: sp.spmatrix, y: np.ndarray, x0: np.ndarray, n_iter: int, with_loglik
             ll.append(loglik(a, x, y))
         x = mlem_step(a, y, x, s)
     return (x, ll) if with_loglik else x
+
+
+# ---------------------------------------------------------------------------
+# ordered subsets, dual matrix, additive term (paper Sec. 5.3-5.4:
+# OSEM; Eq. (DMOS); Eq. (Sohlberg OSEM))
+# ---------------------------------------------------------------------------
+def subset_rows(n_rows: int, rows_per_view: int, n_subsets: int, subset: int) -> np.ndarray:
+    """Rows of views subset, subset + n_subsets, ... (rows are view-major)."""
+    views = np.arange(subset, n_rows // rows_per_view, n_subsets, dtype=np.int64)
+    return (views[:, None] * rows_per_view + np.arange(rows_per_view, dtype=np.int64)[None, :]).ravel()
+
+
+def osem(a_fwd: sp.spmatrix, a_back: sp.spmatrix, subsets, y: np.ndarray, x0: np.ndarray, n_iter: int,
+         add: np.ndarray | None = None) -> np.ndarray:
+    """n_iter sweeps over the row subsets: for each subset S,
+        q = C_S x,  r = y_S / (q + add_S)  (0 where not positive),
+        x <- x / (B_S^T 1) * B_S^T r      (0 where B_S^T 1 = 0),
+    with C = a_fwd (reprojection) and B = a_back (back-projection)."""
+    c = sp.csr_matrix(a_fwd, dtype=np.float64)
+    b = sp.csr_matrix(a_back, dtype=np.float64)
+    y = np.asarray(y, np.float64)
+    ad = np.zeros_like(y) if add is None else np.asarray(add, np.float64)
+    x = np.asarray(x0, np.float64).copy()
+    parts = [(c[rows], b[rows], rows) for rows in subsets]
+    for _ in range(n_iter):
+        for cs, bs, rows in parts:
+            den = cs @ x + ad[rows]
+            r = np.zeros_like(den)
+            np.divide(y[rows], den, out=r, where=den > 0)
+            sb = np.asarray(bs.sum(axis=0), dtype=np.float64).ravel()
+            t = bs.T @ r
+            out = np.zeros_like(x)
+            np.divide(x * t, sb, out=out, where=sb > 0)
+            x = out
+    return x

@@ -72,6 +72,7 @@ typedef struct {
   double hole_len_mm, hole_diam_mm;
   double fwhm_mm;
   double e0_kev, window_frac, photo_k;
+  int32_t primary_only; /* 1: tally only photons that never scattered */
 } orc_problem;
 
 typedef struct {
@@ -354,7 +355,9 @@ static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double
     memset(rec, 0, sizeof(*rec));
     rec->fate = (uint8_t)fate;
   }
-  if (fate == ORC_FATE_ESCAPE) detect(pb, &s, p, d, emit, ctx);
+  /* Sec. 5.3 (dual-matrix OS): the back-projection matrix models attenuation
+   * and detector blur only, i.e. photons that reach the camera unscattered */
+  if (fate == ORC_FATE_ESCAPE && !(pb->primary_only && c.n_compton > 0)) detect(pb, &s, p, d, emit, ctx);
   if (rec) {
     rec->n_virtual = c.n_virtual;
     rec->n_real = c.n_real;

@@ -61,6 +61,8 @@ int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s);
 int sensitivity(const mc_system *sys, double *out, cudaStream_t s);
 int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s);
 int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll, cudaStream_t s);
+int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const float *y, const float *add, float *x,
+             int n_iter, cudaStream_t s);
 int forward_blocks(const mc_system *sys);
 void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
                           std::vector<float> &sig_tab);
@@ -112,6 +114,7 @@ static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
     return MC_EINVAL;
   }
   if (g->precision != MC_FP32 && g->precision != MC_FP64) { set_error("precision must be MC_FP32 or MC_FP64"); return MC_EINVAL; }
+  if (g->tally != MC_TALLY_ALL && g->tally != MC_TALLY_PRIMARY) { set_error("tally must be MC_TALLY_ALL or MC_TALLY_PRIMARY"); return MC_EINVAL; }
   if (ph) {
     const double hx = 0.5 * ph->nx * ph->voxel_mm, hy = 0.5 * ph->ny * ph->voxel_mm;
     if (!(g->radius_mm > std::sqrt(hx * hx + hy * hy))) {
@@ -150,6 +153,7 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
   ts.hole_len = g->hole_len_mm; ts.hole_diam = g->hole_diam_mm; ts.fwhm = g->fwhm_mm;
   ts.e0 = g->e0_kev; ts.window = g->window_frac; ts.photo_k = g->photo_k;
   ts.precision = g->precision;
+  ts.primary_only = g->tally == MC_TALLY_PRIMARY ? 1 : 0;
   const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
   MCS_TRY(pl.material.alloc(nv, s));
   MCS_CUDA(cudaMemcpyAsync(pl.material.p, ph->material_host, nv, cudaMemcpyHostToDevice, s));
@@ -211,6 +215,7 @@ static int pick_group(double mean_len) {
 
 // Work vectors and projector values of a freshly assembled system.
 static int finish_system(mc_system *sys, cudaStream_t s) {
+  if (sys->parent_rows == 0) sys->parent_rows = sys->n_rows;
   MCS_TRY(make_values(sys, s));
   MCS_TRY(sys->xs.alloc((size_t)(sys->n_cols > 0 ? sys->n_cols : 1) * sizeof(float), s));
   MCS_TRY(sys->r.alloc((size_t)(sys->n_rows > 0 ? sys->n_rows : 1) * sizeof(float), s));
@@ -577,6 +582,53 @@ int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_ite
     MCS_CUDA(cudaStreamSynchronize(s));
   }
   return MC_OK;
+}
+
+int mc_system_subset(const mc_system *parent, int64_t rows_per_view, int32_t n_subsets, int32_t subset, void *stream,
+                     mc_system **out) {
+  clear_error();
+  if (!parent || !out) { set_error("NULL argument"); return MC_EINVAL; }
+  *out = nullptr;
+  if (parent->row_map.p) { set_error("the parent is itself a subset"); return MC_EINVAL; }
+  if (rows_per_view < 1 || parent->n_rows % rows_per_view != 0) {
+    set_error("rows_per_view must divide the %lld rows", (long long)parent->n_rows);
+    return MC_EINVAL;
+  }
+  const int64_t V = parent->n_rows / rows_per_view;
+  if (n_subsets < 1 || n_subsets > V || subset < 0 || subset >= n_subsets) {
+    set_error("need 1 <= n_subsets <= %lld views and 0 <= subset < n_subsets", (long long)V);
+    return MC_EINVAL;
+  }
+  cudaStream_t s = API_STREAM(stream);
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  int rc = subset_system(parent, rows_per_view, n_subsets, subset, sys, s);
+  if (rc == MC_OK) rc = finish_system(sys, s);
+  if (rc != MC_OK) { delete sys; return rc; }
+  *out = sys;
+  return MC_OK;
+}
+
+int osem_iterate(mc_system *const *fwd, mc_system *const *back, int32_t n_subsets, const float *y_dev,
+                 const float *add_dev, float *x_dev, int32_t n_iter, void *stream) {
+  clear_error();
+  if (!fwd || !back || !y_dev || !x_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  if (n_subsets < 1 || n_iter < 0) { set_error("n_subsets must be >= 1 and n_iter >= 0"); return MC_EINVAL; }
+  for (int k = 0; k < n_subsets; ++k) {
+    const mc_system *f = fwd[k], *b = back[k];
+    if (!f || !b) { set_error("subset %d: NULL system", k); return MC_EINVAL; }
+    if (f->n_subsets != n_subsets || b->n_subsets != n_subsets || f->subset != k || b->subset != k) {
+      set_error("subset %d: systems must be subset %d of %d (got %d of %d and %d of %d)", k, k, n_subsets, f->subset,
+                f->n_subsets, b->subset, b->n_subsets);
+      return MC_EINVAL;
+    }
+    if (f->n_rows != b->n_rows || f->n_cols != b->n_cols || f->parent_rows != fwd[0]->parent_rows ||
+        b->parent_rows != fwd[0]->parent_rows || f->n_cols != fwd[0]->n_cols) {
+      set_error("subset %d: forward and back-projection systems differ in shape", k);
+      return MC_EINVAL;
+    }
+  }
+  return osem_run(fwd, back, n_subsets, y_dev, add_dev, x_dev, n_iter, API_STREAM(stream));
 }
 
 int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,

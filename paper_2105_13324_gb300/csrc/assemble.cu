@@ -442,3 +442,132 @@ int make_values(mc_system *sys, cudaStream_t s) {
 }
 
 }  // namespace mcs
+
+// ---------------------------------------------------------------------------
+// subset systems (ordered subsets of views, Sec. 5.3)
+// ---------------------------------------------------------------------------
+namespace mcs {
+
+// row i of the subset = row map[i] of the parent: view subset + (i / rpv) * n_sub
+__global__ void subset_rows_kernel(int64_t m_s, int64_t rpv, int n_sub, int subset, const uint32_t *parent_ptr,
+                                   uint32_t *map, uint32_t *len) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_s; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t view = subset + (i / rpv) * n_sub;
+    const uint32_t r = (uint32_t)(view * rpv + i % rpv);
+    map[i] = r;
+    len[i] = parent_ptr[r + 1] - parent_ptr[r];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) len[m_s] = 0u;
+}
+
+// copy the parent's entries of each subset row; emit (col * m_s + i, count)
+__global__ void subset_copy_kernel(int64_t m_s, const uint32_t *map, const uint32_t *parent_ptr,
+                                   const uint32_t *parent_col, const uint32_t *parent_cnt, const uint32_t *ptr,
+                                   uint32_t *col, uint32_t *cnt, uint64_t *tkeys) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_s; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t src = parent_ptr[map[i]], dst = ptr[i], n = ptr[i + 1] - ptr[i];
+    for (uint32_t k = 0; k < n; ++k) {
+      const uint32_t c = parent_col[src + k];
+      col[dst + k] = c;
+      cnt[dst + k] = parent_cnt[src + k];
+      tkeys[dst + k] = (uint64_t)c * (uint64_t)m_s + (uint64_t)i;
+    }
+  }
+}
+
+__global__ void sum_counts_kernel(const uint32_t *cnt, int64_t n, unsigned long long *out) {
+  unsigned long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += cnt[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+int subset_system(const mc_system *parent, int64_t rpv, int n_sub, int subset, mc_system *sys, cudaStream_t s) {
+  const int64_t V = parent->n_rows / rpv;
+  const int64_t nv_s = (V - subset + n_sub - 1) / n_sub;
+  const int64_t m_s = nv_s * rpv, N = parent->n_cols;
+  sys->n_rows = m_s;
+  sys->n_cols = N;
+  sys->first = parent->first;
+  sys->count = parent->count;
+  sys->parent_rows = parent->n_rows;
+  sys->n_subsets = n_sub;
+  sys->subset = subset;
+  MCS_TRY(sys->row_map.alloc((size_t)m_s * sizeof(uint32_t), s));
+  DevBuf len;
+  MCS_TRY(len.alloc((size_t)(m_s + 1) * sizeof(uint32_t), s));
+  MCS_TRY(sys->row_ptr.alloc((size_t)(m_s + 1) * sizeof(uint32_t), s));
+  count_launch();
+  subset_rows_kernel<<<grid_for(m_s), 256, 0, s>>>(m_s, rpv, n_sub, subset, parent->row_ptr.as<uint32_t>(),
+                                                  sys->row_map.as<uint32_t>(), len.as<uint32_t>());
+  MCS_LAUNCHED();
+  MCS_TRY(exclusive_scan_u32(len.as<uint32_t>(), sys->row_ptr.as<uint32_t>(), m_s + 1, s));
+  uint32_t nnz = 0;
+  MCS_CUDA(cudaMemcpyAsync(&nnz, sys->row_ptr.as<uint32_t>() + m_s, 4, cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  sys->nnz = nnz;
+  const size_t nb = (size_t)(nnz > 0 ? nnz : 1);
+  DevBuf tkeys, tkeys_alt, tcnt, tcnt_alt;
+  MCS_TRY(sys->col_idx.alloc(nb * 4, s));
+  MCS_TRY(sys->csr_cnt.alloc(nb * 4, s));
+  MCS_TRY(tkeys.alloc(nb * 8, s));
+  MCS_TRY(tkeys_alt.alloc(nb * 8, s));
+  MCS_TRY(tcnt.alloc(nb * 4, s));
+  MCS_TRY(tcnt_alt.alloc(nb * 4, s));
+  count_launch();
+  subset_copy_kernel<<<grid_for(m_s), 256, 0, s>>>(m_s, sys->row_map.as<uint32_t>(), parent->row_ptr.as<uint32_t>(),
+                                                  parent->col_idx.as<uint32_t>(), parent->csr_cnt.as<uint32_t>(),
+                                                  sys->row_ptr.as<uint32_t>(), sys->col_idx.as<uint32_t>(),
+                                                  sys->csr_cnt.as<uint32_t>(), tkeys.as<uint64_t>());
+  MCS_LAUNCHED();
+  // CSC of the subset: sort (col * m_s + row, count)
+  MCS_CUDA(cudaMemcpyAsync(tcnt.p, sys->csr_cnt.p, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+  bool alt = false;
+  MCS_TRY(radix_sort_u64(tkeys.as<uint64_t>(), tkeys_alt.as<uint64_t>(), tcnt.as<uint32_t>(), tcnt_alt.as<uint32_t>(),
+                         nnz, bits_for((uint64_t)m_s * (uint64_t)N - 1), &alt, s));
+  const uint64_t *tk = alt ? tkeys_alt.as<uint64_t>() : tkeys.as<uint64_t>();
+  const uint32_t *tc = alt ? tcnt_alt.as<uint32_t>() : tcnt.as<uint32_t>();
+  DevBuf hist;
+  MCS_TRY(hist.alloc((size_t)(N + 1) * 4, s));
+  MCS_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)(N + 1) * 4, s));
+  MCS_TRY(sys->col_ptr.alloc((size_t)(N + 1) * 4, s));
+  MCS_TRY(sys->row_idx.alloc(nb * 4, s));
+  MCS_TRY(sys->csc_cnt.alloc(nb * 4, s));
+  if (nnz > 0) {
+    count_launch();
+    split_keys_kernel<<<grid_for(nnz), 256, 0, s>>>(tk, nnz, (uint64_t)m_s, nullptr, sys->row_idx.as<uint32_t>(),
+                                                    hist.as<uint32_t>());
+    MCS_LAUNCHED();
+    MCS_CUDA(cudaMemcpyAsync(sys->csc_cnt.p, tc, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), N + 1, s));
+  // histories per voxel are the parent's; column sums and largest count
+  MCS_TRY(sys->n_v.alloc((size_t)N * 4, s));
+  MCS_TRY(sys->inv_n.alloc((size_t)N * 4, s));
+  MCS_CUDA(cudaMemcpyAsync(sys->n_v.p, parent->n_v.p, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(sys->inv_n.p, parent->inv_n.p, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+  MCS_TRY(sys->colsum.alloc((size_t)N * sizeof(double), s));
+  MCS_TRY(sys->inv_colsum.alloc((size_t)N * sizeof(float), s));
+  DevBuf mx;
+  MCS_TRY(mx.alloc(2 * sizeof(unsigned long long), s));
+  MCS_CUDA(cudaMemsetAsync(mx.p, 0, 2 * sizeof(unsigned long long), s));
+  count_launch();
+  column_sums_kernel<<<grid_for(N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(), N,
+                                                 sys->colsum.as<double>(), sys->inv_colsum.as<float>(),
+                                                 mx.as<unsigned int>());
+  count_launch();
+  sum_counts_kernel<<<grid_for(nnz > 0 ? nnz : 1), 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), nnz,
+                                                                mx.as<unsigned long long>() + 1);
+  MCS_LAUNCHED();
+  unsigned long long h[2] = {0, 0};
+  MCS_CUDA(cudaMemcpyAsync(h, mx.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  sys->max_count = (uint32_t)(h[0] & 0xFFFFFFFFull);
+  sys->n_events = (int64_t)h[1];
+  for (int f = 0; f < 4; ++f) sys->fates[f] = parent->fates[f];
+  return MC_OK;
+}
+
+}  // namespace mcs

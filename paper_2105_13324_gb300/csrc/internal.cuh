@@ -116,6 +116,11 @@ struct mc_system {
   mcs::DevBuf csr_blocks, csc_blocks;  // u32 [n_blocks + 1] first row / column of each tile
   int64_t n_csr_blocks = 0, n_csc_blocks = 0;
   bool warp_rows_fwd = false, warp_rows_bwd = false;
+  // ordered subsets: row i of this system is row row_map[i] of its parent
+  // (empty for a full system)
+  mcs::DevBuf row_map;
+  int64_t parent_rows = 0;
+  int32_t n_subsets = 1, subset = 0;
 };
 
 namespace mcs {
@@ -154,6 +159,7 @@ struct TransportSetup {
   unsigned long long *esc_cursor;
   cudaEvent_t ev_mid;          // recorded between transport and detection (optional)
   int precision;
+  int primary_only;            // tally only unscattered photons
 };
 
 // bytes of one escape-queue entry for a precision
@@ -171,6 +177,10 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s);
 
 // Projector value arrays for sys->value_type.
 int make_values(mc_system *sys, cudaStream_t s);
+
+// System of the rows of views subset, subset + n_sub, ... of a parent whose
+// rows are view-major with rpv rows per view (assemble.cu).
+int subset_system(const mc_system *parent, int64_t rpv, int n_sub, int subset, mc_system *sys, cudaStream_t s);
 
 // Tile partition of CSR and CSC for the streaming SpMV kernels (mlem.cu).
 int make_stream_blocks(mc_system *sys, cudaStream_t s);

@@ -107,13 +107,28 @@ __device__ __forceinline__ float segment_dot(uint32_t b, uint32_t e, const uint3
 
 // MODE 0: out = q.  MODE 1: out = r = y / q (0 where q = 0), and with LL the
 // block's share of sum_j (y_j ln q_j - q_j) in partials[blockIdx.x].
+// MODE 2: r_i = y_o / (q_i + add_o), o = rmap[i] (i without a map), 0 where
+// the denominator is not positive (Eq. (Sohlberg OSEM) of Sec. 5.4).
+template <int MODE>
+__device__ __forceinline__ float ratio_out(float acc, int64_t i, const float *y, const uint32_t *rmap, const float *add) {
+  if (MODE == 1) {
+    const float yj = y[i];
+    return acc > 0.0f ? yj / acc : 0.0f;
+  }
+  const int64_t o = rmap ? (int64_t)rmap[i] : i;
+  const float den = acc + (add ? add[o] : 0.0f);
+  return den > 0.0f ? y[o] / den : 0.0f;
+}
+
 template <typename V, int G, int MODE, bool LL>
 __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_t *__restrict__ row_ptr,
                                                                    const uint32_t *__restrict__ col,
                                                                    const V *__restrict__ val,
                                                                    const float *__restrict__ xs, int64_t m,
                                                                    const float *__restrict__ y,
-                                                                   float *__restrict__ out, double *partials) {
+                                                                   float *__restrict__ out, double *partials,
+                                                                   const uint32_t *__restrict__ rmap,
+                                                                   const float *__restrict__ add) {
   __shared__ double s_tmp[kSpmvThreads / 32];
   const int64_t gid = ((int64_t)blockIdx.x * kSpmvThreads + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
@@ -129,9 +144,11 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
     if (MODE == 0) {
       out[gid] = acc;
     } else {
-      const float yj = y[gid];
-      out[gid] = acc > 0.0f ? yj / acc : 0.0f;
-      if (LL) ll = (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+      out[gid] = ratio_out<MODE>(acc, gid, y, rmap, add);
+      if (LL) {
+        const float yj = y[gid];
+        ll = (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+      }
     }
   }
   if (LL) {
@@ -261,7 +278,9 @@ __global__ void __launch_bounds__(kStreamThreads) stream_forward_kernel(const ui
                                                                      const V *__restrict__ val,
                                                                      const float *__restrict__ xs,
                                                                      const float *__restrict__ y,
-                                                                     float *__restrict__ out, double *partials) {
+                                                                     float *__restrict__ out, double *partials,
+                                                                     const uint32_t *__restrict__ rmap,
+                                                                     const float *__restrict__ add) {
   __shared__ float s_prod[kStreamTile];
   __shared__ double s_tmp[kStreamThreads / 32];
   const uint32_t r0 = tiles[blockIdx.x], r1 = tiles[blockIdx.x + 1];
@@ -277,9 +296,11 @@ __global__ void __launch_bounds__(kStreamThreads) stream_forward_kernel(const ui
       if (MODE == 0) {
         out[r] = acc;
       } else {
-        const float yj = y[r];
-        out[r] = acc > 0.0f ? yj / acc : 0.0f;
-        if (LL) ll += (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+        out[r] = ratio_out<MODE>(acc, r, y, rmap, add);
+        if (LL) {
+          const float yj = y[r];
+          ll += (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+        }
       }
     }
   }
@@ -363,18 +384,18 @@ static int grid_stride_blocks(int64_t n) {
 
 template <typename V, int MODE, bool LL>
 static void fwd_launch(const mc_system *sys, int g, const float *xs, const float *y, float *out, double *partials,
-                       cudaStream_t s) {
+                       cudaStream_t s, const uint32_t *rmap = nullptr, const float *add = nullptr) {
   const int64_t m = sys->n_rows;
   const int blocks = div_up(m * g, kSpmvThreads);
   const V *val = sys->csr_val.as<V>();
   const uint32_t *rp = sys->row_ptr.as<uint32_t>(), *ci = sys->col_idx.as<uint32_t>();
   switch (g) {
-    case 1: count_launch(); csr_forward_kernel<V, 1, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
-    case 2: count_launch(); csr_forward_kernel<V, 2, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
-    case 4: count_launch(); csr_forward_kernel<V, 4, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
-    case 8: count_launch(); csr_forward_kernel<V, 8, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
-    case 16: count_launch(); csr_forward_kernel<V, 16, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
-    default: count_launch(); csr_forward_kernel<V, 32, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials); break;
+    case 1: count_launch(); csr_forward_kernel<V, 1, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 2: count_launch(); csr_forward_kernel<V, 2, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 4: count_launch(); csr_forward_kernel<V, 4, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 8: count_launch(); csr_forward_kernel<V, 8, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 16: count_launch(); csr_forward_kernel<V, 16, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    default: count_launch(); csr_forward_kernel<V, 32, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
   }
 }
 
@@ -397,15 +418,17 @@ static void back_launch(const mc_system *sys, int g, const float *r, float *x, f
 
 template <typename V, int MODE, bool LL>
 static void stream_fwd_launch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
-                              cudaStream_t s) {
+                              cudaStream_t s, const uint32_t *rmap = nullptr, const float *add = nullptr) {
   const unsigned nb = (unsigned)sys->n_csr_blocks;
   const uint32_t *rp = sys->row_ptr.as<uint32_t>(), *t = sys->csr_blocks.as<uint32_t>(), *ci = sys->col_idx.as<uint32_t>();
   const V *val = sys->csr_val.as<V>();
   count_launch();
   if (sys->warp_rows_fwd)
-    stream_forward_kernel<V, true, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials);
+    stream_forward_kernel<V, true, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials,
+                                                                            rmap, add);
   else
-    stream_forward_kernel<V, false, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials);
+    stream_forward_kernel<V, false, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials,
+                                                                             rmap, add);
 }
 
 template <typename V, int MODE>
@@ -423,17 +446,18 @@ static void stream_back_launch(const mc_system *sys, const float *r, float *x, f
 
 template <int MODE, bool LL>
 static void fwd_dispatch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
-                         cudaStream_t s) {
+                         cudaStream_t s, const uint32_t *rmap = nullptr, const float *add = nullptr) {
   if (sys->n_csr_blocks > 0) {
-    if (sys->value_type == MC_VAL_F16) stream_fwd_launch<__half, MODE, LL>(sys, xs, y, out, partials, s);
-    else if (sys->value_type == MC_VAL_BF16) stream_fwd_launch<__nv_bfloat16, MODE, LL>(sys, xs, y, out, partials, s);
-    else stream_fwd_launch<float, MODE, LL>(sys, xs, y, out, partials, s);
+    if (sys->value_type == MC_VAL_F16) stream_fwd_launch<__half, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
+    else if (sys->value_type == MC_VAL_BF16)
+      stream_fwd_launch<__nv_bfloat16, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
+    else stream_fwd_launch<float, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
     return;
   }
   const int g = sys->spmv_group_fwd;
-  if (sys->value_type == MC_VAL_F16) fwd_launch<__half, MODE, LL>(sys, g, xs, y, out, partials, s);
-  else if (sys->value_type == MC_VAL_BF16) fwd_launch<__nv_bfloat16, MODE, LL>(sys, g, xs, y, out, partials, s);
-  else fwd_launch<float, MODE, LL>(sys, g, xs, y, out, partials, s);
+  if (sys->value_type == MC_VAL_F16) fwd_launch<__half, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
+  else if (sys->value_type == MC_VAL_BF16) fwd_launch<__nv_bfloat16, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
+  else fwd_launch<float, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
 }
 
 template <int MODE>
@@ -532,6 +556,30 @@ int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s) {
                                                                      sys->xs.as<float>());
   }
   MCS_LAUNCHED();
+  return MC_OK;
+}
+
+// Ordered-subset EM sweeps: for each subset s, forward with fwd[s] (ratio
+// with the additive term and the subset's row map), back-projection and
+// update with back[s] (its column sums).  fwd and back may differ (dual
+// matrix, Eq. (DMOS)); one subset with fwd = back is ML-EM.
+int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const float *y, const float *add, float *x,
+             int n_iter, cudaStream_t s) {
+  for (int it = 0; it < n_iter; ++it) {
+    for (int k = 0; k < n_sub; ++k) {
+      mc_system *f = fwd[k], *b = back[k];
+      const int64_t n = f->n_cols;
+      if (n > 0) {
+        count_launch();
+        prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, f->inv_n.as<float>(), f->xs.as<float>(), n);
+      }
+      if (f->n_rows > 0)
+        fwd_dispatch<2, false>(f, f->xs.as<float>(), y, f->r.as<float>(), nullptr, s,
+                               f->row_map.p ? f->row_map.as<uint32_t>() : nullptr, add);
+      if (n > 0) back_dispatch<1>(b, f->r.as<float>(), x, b->xs.as<float>(), s);
+      MCS_LAUNCHED();
+    }
+  }
   return MC_OK;
 }
 

@@ -57,6 +57,7 @@ template <typename T> struct TArgs {
   T start_deg, inv_delta, psi_views;  // azimuth window of candidate views
   int views_per_turn;                 // 360 / delta if integral, else 0
   int t_coll, t_emit;                 // lanes that must wait before a warp runs collisions / emissions
+  int primary_only;                   // tally only photons that never scattered
   T sigma, plane, bin, half_bu, half_bv;
   int n_views, bins_u, bins_v;
   uint32_t n_vox;
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       }
     }
     if (fate >= 0) {
-      if (fate == MC_FATE_ESCAPE && fabs(dz) < a.w_max) {
+      if (fate == MC_FATE_ESCAPE && fabs(dz) < a.w_max && !(a.primary_only && n_compton > 0)) {
         // a view may accept it: queue it for the detection kernel
         cg::coalesced_group g = cg::coalesced_threads();
         unsigned long long base = 0;
@@ -833,6 +834,7 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.first = ts.first; a.count = ts.count;
   a.events = ts.events; a.capacity = ts.capacity; a.cursor = ts.cursor; a.fates = ts.fates;
   a.records = ts.records;
+  a.primary_only = ts.primary_only;
   a.t_coll = kWaitCollide;
   a.t_emit = kWaitEmit;
   a.esc = ts.esc;

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EFORMAT = 0, -1, -2, -3, -4, -5
 MC_FP32, MC_FP64 = 0, 1
 MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
+MC_TALLY_ALL, MC_TALLY_PRIMARY = 0, 1
 FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 
 # every symbol include/mcspect.h declares
@@ -30,6 +31,7 @@ EXPORTED = (
     "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
+    "mc_system_subset", "osem_iterate",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
 )
 
@@ -59,7 +61,8 @@ class MCGeometry(ctypes.Structure):
                 ("n_bins_u", ctypes.c_int32), ("n_bins_v", ctypes.c_int32), ("bin_mm", ctypes.c_double),
                 ("radius_mm", ctypes.c_double), ("hole_len_mm", ctypes.c_double),
                 ("hole_diam_mm", ctypes.c_double), ("fwhm_mm", ctypes.c_double), ("e0_kev", ctypes.c_double),
-                ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double), ("precision", ctypes.c_int32)]
+                ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("tally", ctypes.c_int32)]
 
 
 class MCSystemInfo(ctypes.Structure):
@@ -103,6 +106,8 @@ def load(path: str | None = None):
             "mc_mlem_init": [vp, vp, vp, vp],
             "mlem_iterate": [vp, vp, vp, i32, vp, vp],
             "mlem_iterate_noalloc": [vp, vp, vp, i32, vp, vp],
+            "mc_system_subset": [vp, i64, i32, i32, vp, vp],
+            "osem_iterate": [vp, vp, i32, vp, vp, vp, i32, vp],
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
             "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
@@ -144,7 +149,7 @@ def _dev_ptr(t, dtype=None):
 class _Inputs:
     """C structs for a Phantom + Geometry, keeping NumPy buffers alive."""
 
-    def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int):
+    def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int, primary_only: bool = False):
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -156,7 +161,7 @@ class _Inputs:
         self.geo = MCGeometry(g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
                               float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
                               float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
-                              int(precision))
+                              int(precision), int(bool(primary_only)))
 
 
 def _precision(p):
@@ -233,8 +238,8 @@ class System:
 class Plan:
     """Owner of an mc_plan handle: phantom + geometry resident on the device."""
 
-    def __init__(self, phantom, geometry, precision="fp32", stream=None):
-        inp = _Inputs(phantom, geometry, _precision(precision))
+    def __init__(self, phantom, geometry, precision="fp32", stream=None, primary_only=False):
+        inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
         h = ctypes.c_void_p()
         _check(load().mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), _stream_ptr(stream),
                                      ctypes.byref(h)))
@@ -257,8 +262,8 @@ class Plan:
             pass
 
 
-def mc_plan_create(phantom, geometry, precision="fp32", stream=None) -> Plan:
-    return Plan(phantom, geometry, precision, stream)
+def mc_plan_create(phantom, geometry, precision="fp32", stream=None, primary_only=False) -> Plan:
+    return Plan(phantom, geometry, precision, stream, primary_only)
 
 
 def mc_plan_build(plan: Plan, first: int, count: int, seed: int, stream=None) -> System:
@@ -277,8 +282,9 @@ def mc_kernel_launches() -> int:
     return int(load().mc_kernel_launches())
 
 
-def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="fp32", stream=None) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision))
+def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="fp32", stream=None,
+                    primary_only=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
     h = ctypes.c_void_p()
     _check(load().mc_build_system(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(n_histories), int(seed),
                                   _stream_ptr(stream), ctypes.byref(h)))
@@ -286,8 +292,8 @@ def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="f
 
 
 def mc_build_system_range(phantom, geometry, first: int, count: int, seed: int, precision="fp32",
-                          stream=None) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision))
+                          stream=None, primary_only=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
     h = ctypes.c_void_p()
     _check(load().mc_build_system_range(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(first), int(count),
                                         int(seed), _stream_ptr(stream), ctypes.byref(h)))
@@ -351,8 +357,29 @@ def mlem_iterate_noalloc(sys: System, y, x, n_iter: int, loglik: bool = False, s
     return ll[:n_iter] if loglik else None
 
 
-def mc_trace_histories(phantom, geometry, seed: int, first: int, count: int, precision="fp64") -> np.ndarray:
-    inp = _Inputs(phantom, geometry, _precision(precision))
+def mc_system_subset(parent: System, rows_per_view: int, n_subsets: int, subset: int, stream=None) -> System:
+    h = ctypes.c_void_p()
+    _check(load().mc_system_subset(parent.handle, int(rows_per_view), int(n_subsets), int(subset),
+                                   _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def osem_iterate(fwd, back, y, x, n_iter: int, add=None, stream=None):
+    """n_iter ordered-subset EM sweeps; fwd/back: lists of subset systems."""
+    import torch
+    if len(fwd) != len(back) or not fwd:
+        raise ValueError("fwd and back need the same, non-zero number of subsets")
+    arr = (ctypes.c_void_p * len(fwd))(*[f.handle for f in fwd])
+    brr = (ctypes.c_void_p * len(back))(*[b.handle for b in back])
+    _check(load().osem_iterate(arr, brr, len(fwd), _dev_ptr(y, torch.float32),
+                               _dev_ptr(add, torch.float32) if add is not None else None,
+                               _dev_ptr(x, torch.float32), int(n_iter), _stream_ptr(stream)))
+    return x
+
+
+def mc_trace_histories(phantom, geometry, seed: int, first: int, count: int, precision="fp64",
+                       primary_only=False) -> np.ndarray:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
     out = np.zeros(count, RECORD_DTYPE)
     _check(load().mc_trace_histories(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(seed), int(first),
                                      int(count), out.ctypes.data))
