@@ -223,12 +223,14 @@ MC_API int mc_system_subset(const mc_system *parent, int64_t rows_per_view, int3
  * place on x_dev[N]: for s = 0 .. n_subsets-1,
  *   q = C_s x,  r_i = y_o / (q_i + add_o) (0 if not positive), o the parent
  *   row of subset row i,
- *   x_v <- x_v / sum_i B_s,iv * sum_i B_s,iv r_i   (x_v = 0 where the sum is 0)
+ *   x_v <- x_v / sum_i B_s,iv * sum_i B_s,iv r_i   (x_v kept where the sum is
+ *   0: the voxel is outside subset s's view)
  * with C_s = fwd[s] (reprojection, e.g. all photons) and B_s = back[s]
  * (back-projection, e.g. MC_TALLY_PRIMARY).  fwd[s] and back[s] must be
  * subset s of n_subsets (n_subsets = 1: full systems) of the same shape.
  * y_dev and add_dev (nullable: no additive term) have the parent's rows.
- * fwd = back with one subset and no additive term is mlem_iterate. */
+ * fwd = back with one subset and no additive term is mlem_iterate from a
+ * start image that is 0 off the support (as mc_mlem_init gives). */
 MC_API int osem_iterate(mc_system *const *fwd, mc_system *const *back, int32_t n_subsets, const float *y_dev,
                         const float *add_dev, float *x_dev, int32_t n_iter, void *stream);
 

@@ -332,7 +332,8 @@ def osem(a_fwd: sp.spmatrix, a_back: sp.spmatrix, subsets, y: np.ndarray, x0: np
          add: np.ndarray | None = None) -> np.ndarray:
     """n_iter sweeps over the row subsets: for each subset S,
         q = C_S x,  r = y_S / (q + add_S)  (0 where not positive),
-        x <- x / (B_S^T 1) * B_S^T r      (0 where B_S^T 1 = 0),
+        x <- x / (B_S^T 1) * B_S^T r      (x kept where B_S^T 1 = 0: the
+                                           voxel is outside the subset's view),
     with C = a_fwd (reprojection) and B = a_back (back-projection)."""
     c = sp.csr_matrix(a_fwd, dtype=np.float64)
     b = sp.csr_matrix(a_back, dtype=np.float64)
@@ -347,7 +348,7 @@ def osem(a_fwd: sp.spmatrix, a_back: sp.spmatrix, subsets, y: np.ndarray, x0: np
             np.divide(y[rows], den, out=r, where=den > 0)
             sb = np.asarray(bs.sum(axis=0), dtype=np.float64).ravel()
             t = bs.T @ r
-            out = np.zeros_like(x)
+            out = x.copy()      # a voxel the subset does not see keeps its value
             np.divide(x * t, sb, out=out, where=sb > 0)
             x = out
     return x

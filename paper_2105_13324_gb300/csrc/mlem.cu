@@ -159,6 +159,8 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
 
 // MODE 0: out_v = (1/n_v) sum_j C_jv r_j (back-projection A^T r).
 // MODE 1: x_v <- x_v t_v / S_v (0 where S_v = 0), xs_v = x_v / n_v.
+// MODE 3: as MODE 1 but x_v is kept where S_v = 0 (a voxel outside an
+// ordered subset's view is not updated by that subset).
 template <typename V, int G, int MODE>
 __global__ void __launch_bounds__(kSpmvThreads) csc_back_kernel(const uint32_t *__restrict__ col_ptr,
                                                                 const uint32_t *__restrict__ row,
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(kSpmvThreads) csc_back_kernel(const uint32_t *
       x[gid] = acc * inv_n[gid];
     } else {
       const float is = inv_colsum[gid];
-      const float xn = is > 0.0f ? x[gid] * acc * is : 0.0f;
+      const float xn = is > 0.0f ? x[gid] * acc * is : (MODE == 3 ? x[gid] : 0.0f);
       x[gid] = xn;
       xs[gid] = xn * inv_n[gid];
     }
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_back_kernel(const uint3
         x[v] = acc * inv_n[v];
       } else {
         const float is = inv_colsum[v];
-        const float xn = is > 0.0f ? x[v] * acc * is : 0.0f;
+        const float xn = is > 0.0f ? x[v] * acc * is : (MODE == 3 ? x[v] : 0.0f);
         x[v] = xn;
         xs[v] = xn * inv_n[v];
       }
@@ -561,7 +563,8 @@ int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s) {
 
 // Ordered-subset EM sweeps: for each subset s, forward with fwd[s] (ratio
 // with the additive term and the subset's row map), back-projection and
-// update with back[s] (its column sums).  fwd and back may differ (dual
+// update with back[s] (its column sums; voxels the subset does not see keep
+// their value).  fwd and back may differ (dual
 // matrix, Eq. (DMOS)); one subset with fwd = back is ML-EM.
 int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const float *y, const float *add, float *x,
              int n_iter, cudaStream_t s) {
@@ -576,7 +579,7 @@ int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const flo
       if (f->n_rows > 0)
         fwd_dispatch<2, false>(f, f->xs.as<float>(), y, f->r.as<float>(), nullptr, s,
                                f->row_map.p ? f->row_map.as<uint32_t>() : nullptr, add);
-      if (n > 0) back_dispatch<1>(b, f->r.as<float>(), x, b->xs.as<float>(), s);
+      if (n > 0) back_dispatch<3>(b, f->r.as<float>(), x, b->xs.as<float>(), s);
       MCS_LAUNCHED();
     }
   }

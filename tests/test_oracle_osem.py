@@ -78,3 +78,13 @@ def test_primary_only_matrix_is_the_unscattered_part():
     f0 = oracle.build_system(oracle.Problem(ph, g), 3, 300_000)[1]
     p0 = oracle.build_system(oracle.Problem(ph, g, primary_only=True), 3, 300_000)[1]
     assert (f0 != p0).nnz == 0 and f0.nnz > 0
+
+
+def test_voxels_outside_a_subset_keep_their_value():
+    # voxel 2 is seen only by rows of subset 0: subset 1 must not change it
+    a = sp.csr_matrix(np.array([[1.0, 0.0, 1.0], [0.0, 1.0, 0.0], [1.0, 1.0, 0.0], [0.0, 2.0, 0.0]]))
+    y = np.array([2.0, 1.0, 3.0, 2.0])
+    x0 = np.array([1.0, 1.0, 5.0])
+    sub1 = np.array([2, 3])            # rows that do not see voxel 2
+    x = oracle.osem(a, a, [sub1], y, x0, 1)
+    assert x[2] == 5.0
