@@ -189,6 +189,11 @@ MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t 
 /* Forward projection q = A x (Eq. (IMC)): x_dev[N], q_dev[M], float. */
 MC_API int mc_project(const mc_system *sys, const float *x_dev, float *q_dev, void *stream);
 
+/* Ratio of Eq. (MLEM): r_j = y_j / (A x)_j, 0 where (A x)_j = 0:
+ * x_dev[N], y_dev[M], r_dev[M], float.  Uses the system's work vector, like
+ * the other projector calls on one system. */
+MC_API int mc_project_ratio(const mc_system *sys, const float *x_dev, const float *y_dev, float *r_dev, void *stream);
+
 /* Back-projection b = A^T r: r_dev[M], b_dev[N], float. */
 MC_API int mc_backproject(const mc_system *sys, const float *r_dev, float *b_dev, void *stream);
 
@@ -233,6 +238,33 @@ MC_API int mc_system_subset(const mc_system *parent, int64_t rows_per_view, int3
  * start image that is 0 off the support (as mc_mlem_init gives). */
 MC_API int osem_iterate(mc_system *const *fwd, mc_system *const *back, int32_t n_subsets, const float *y_dev,
                         const float *add_dev, float *x_dev, int32_t n_iter, void *stream);
+
+/* Double-precision projectors (same matrix, FP64 accumulation): q = A x and
+ * b = A^T r on double device vectors; for derivative checks and FP64
+ * reference images. */
+MC_API int mc_project_f64(const mc_system *sys, const double *x_dev, double *q_dev, void *stream);
+MC_API int mc_backproject_f64(const mc_system *sys, const double *r_dev, double *b_dev, void *stream);
+
+/* Quadratic 6-neighbour smoothness prior on an nx*ny*nz image (x fastest):
+ *   R(x) = beta/2 sum over neighbouring voxel pairs (x_v - x_w)^2,
+ *   grad_v = beta sum over the 6 (fewer at the border) neighbours (x_v - x_w).
+ * grad_dev (N values) and value_dev (one double) may each be NULL.  The
+ * paper reconstructs by plain ML-EM (Sec. 5.1); this penalty is an addition
+ * for the penalised Poisson likelihood. */
+MC_API int mc_prior_quadratic(int32_t nx, int32_t ny, int32_t nz, double beta, const float *x_dev, float *grad_dev,
+                              double *value_dev, void *stream);
+MC_API int mc_prior_quadratic_f64(int32_t nx, int32_t ny, int32_t nz, double beta, const double *x_dev,
+                                  double *grad_dev, double *value_dev, void *stream);
+
+/* One preconditioned projected-gradient step on the penalised negative
+ * log-likelihood  sum_j (q_j - y_j ln q_j) + R(x)  (Poisson likelihood of
+ * Sec. 5.1), in place on x_dev[n]:
+ *   x_v <- max(0, x_v - alpha (x_v / s_v) (s_v - bp_v + gp_v)),
+ * with s the sensitivity (mc_sensitivity), bp = A^T (y / A x) and gp the
+ * prior gradient (NULL: none); x_v = 0 where s_v = 0.  alpha = 1 without a
+ * prior is one ML-EM update (Eq. (MLEM)). */
+MC_API int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp_dev, const float *gp_dev,
+                       float *x_dev, void *stream);
 
 /* ML-EM like mlem_iterate, for callers that must not allocate device
  * memory: a reconstruction service that plans its memory up front (a device

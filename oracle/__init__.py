@@ -352,3 +352,40 @@ def osem(a_fwd: sp.spmatrix, a_back: sp.spmatrix, subsets, y: np.ndarray, x0: np
             np.divide(x * t, sb, out=out, where=sb > 0)
             x = out
     return x
+
+
+# ---------------------------------------------------------------------------
+# penalised Poisson likelihood (Sec. 5.1 likelihood + quadratic smoothness)
+# ---------------------------------------------------------------------------
+def prior_quadratic(x: np.ndarray, shape, beta: float):
+    """R(x) = beta/2 * sum over 6-neighbour voxel pairs (x_v - x_w)^2 and its
+    gradient, for an image of shape (nz, ny, nx), x fastest."""
+    img = np.asarray(x, np.float64).reshape(shape)
+    val = 0.0
+    grad = np.zeros_like(img)
+    for ax in range(3):
+        d = np.diff(img, axis=ax)            # x_{v+1} - x_v along the axis
+        val += float(np.sum(d * d))
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        grad[tuple(lo)] -= d                 # v gets (x_v - x_{v+1})
+        grad[tuple(hi)] += d                 # v+1 gets (x_{v+1} - x_v)
+    return 0.5 * beta * val, beta * grad.ravel()
+
+
+def penalised_objective(a: sp.spmatrix, y: np.ndarray, x: np.ndarray, shape, beta: float) -> float:
+    """sum_j (q_j - y_j ln q_j) + R(x), q = A x (negative log-likelihood up to
+    a constant, plus the prior)."""
+    q = a @ np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    pos = y > 0
+    return float(np.sum(q) - np.sum(y[pos] * np.log(q[pos])) + prior_quadratic(x, shape, beta)[0])
+
+
+def penalised_gradient(a: sp.spmatrix, y: np.ndarray, x: np.ndarray, shape, beta: float) -> np.ndarray:
+    q = a @ np.asarray(x, np.float64)
+    r = np.zeros_like(q)
+    np.divide(np.asarray(y, np.float64), q, out=r, where=q > 0)
+    return sensitivity(a) - a.T @ r + prior_quadratic(x, shape, beta)[1]

@@ -64,6 +64,12 @@ int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll,
 int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const float *y, const float *add, float *x,
              int n_iter, cudaStream_t s);
 int forward_blocks(const mc_system *sys);
+int project_f64(const mc_system *sys, const double *x, double *q, cudaStream_t s);
+int project_ratio(const mc_system *sys, const float *x, const float *y, float *r, cudaStream_t s);
+int backproject_f64(const mc_system *sys, const double *r, double *b, cudaStream_t s);
+template <typename T>
+int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, double *value, cudaStream_t s);
+int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const float *gp, float *x, cudaStream_t s);
 void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
                           std::vector<float> &sig_tab);
 
@@ -629,6 +635,53 @@ int osem_iterate(mc_system *const *fwd, mc_system *const *back, int32_t n_subset
     }
   }
   return osem_run(fwd, back, n_subsets, y_dev, add_dev, x_dev, n_iter, API_STREAM(stream));
+}
+
+int mc_project_ratio(const mc_system *sys, const float *x_dev, const float *y_dev, float *r_dev, void *stream) {
+  clear_error();
+  if (!sys || !x_dev || !y_dev || !r_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return project_ratio(sys, x_dev, y_dev, r_dev, API_STREAM(stream));
+}
+
+int mc_project_f64(const mc_system *sys, const double *x_dev, double *q_dev, void *stream) {
+  clear_error();
+  if (!sys || !x_dev || !q_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return project_f64(sys, x_dev, q_dev, API_STREAM(stream));
+}
+
+int mc_backproject_f64(const mc_system *sys, const double *r_dev, double *b_dev, void *stream) {
+  clear_error();
+  if (!sys || !r_dev || !b_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return backproject_f64(sys, r_dev, b_dev, API_STREAM(stream));
+}
+
+static int check_prior(int32_t nx, int32_t ny, int32_t nz, double beta, const void *x) {
+  if (!x) { set_error("x is NULL"); return MC_EINVAL; }
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (1ll << 40)) { set_error("bad grid"); return MC_EINVAL; }
+  if (!(beta >= 0.0) || !std::isfinite(beta)) { set_error("beta must be finite and >= 0"); return MC_EINVAL; }
+  return MC_OK;
+}
+
+int mc_prior_quadratic(int32_t nx, int32_t ny, int32_t nz, double beta, const float *x_dev, float *grad_dev,
+                       double *value_dev, void *stream) {
+  clear_error();
+  MCS_TRY(check_prior(nx, ny, nz, beta, x_dev));
+  return prior_quadratic<float>(nx, ny, nz, beta, x_dev, grad_dev, value_dev, API_STREAM(stream));
+}
+
+int mc_prior_quadratic_f64(int32_t nx, int32_t ny, int32_t nz, double beta, const double *x_dev, double *grad_dev,
+                           double *value_dev, void *stream) {
+  clear_error();
+  MCS_TRY(check_prior(nx, ny, nz, beta, x_dev));
+  return prior_quadratic<double>(nx, ny, nz, beta, x_dev, grad_dev, value_dev, API_STREAM(stream));
+}
+
+int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp_dev, const float *gp_dev,
+                float *x_dev, void *stream) {
+  clear_error();
+  if (!sens_dev || !bp_dev || !x_dev || n < 0) { set_error("NULL argument or negative size"); return MC_EINVAL; }
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) { set_error("alpha must be positive"); return MC_EINVAL; }
+  return pgd_step(n, alpha, sens_dev, bp_dev, gp_dev, x_dev, API_STREAM(stream));
 }
 
 int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,

@@ -525,6 +525,18 @@ int project(const mc_system *sys, const float *x, float *q, cudaStream_t s) {
   return MC_OK;
 }
 
+// r = y / (A x), 0 where A x = 0 (the ratio of Eq. (MLEM))
+int project_ratio(const mc_system *sys, const float *x, const float *y, float *r, cudaStream_t s) {
+  if (sys->n_cols > 0) {
+    count_launch();
+    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
+                                                                     sys->n_cols);
+  }
+  if (sys->n_rows > 0) fwd_dispatch<1, false>(sys, sys->xs.as<float>(), y, r, nullptr, s);
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
 int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s) {
   if (sys->n_cols > 0) back_dispatch<0>(sys, r, b, nullptr, s);
   MCS_LAUNCHED();
@@ -708,3 +720,124 @@ extern "C" int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, fl
   }
   return MC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// double-precision projectors, quadratic prior, preconditioned gradient step
+// (the differentiable / penalised forms built on Eq. (IMC) and the Poisson
+// likelihood of Sec. 5.1)
+// ---------------------------------------------------------------------------
+namespace mcs {
+
+// q_j = sum_v C_jv x_v / n_v, one thread per row, double accumulation
+__global__ void forward_f64_kernel(const uint32_t *row_ptr, const uint32_t *col, const uint32_t *cnt,
+                                   const uint32_t *n_v, const double *x, int64_t m, double *q) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (uint32_t k = row_ptr[j]; k < row_ptr[j + 1]; ++k) {
+      const uint32_t v = col[k];
+      acc += (double)cnt[k] * (x[v] / (double)n_v[v]);
+    }
+    q[j] = acc;
+  }
+}
+
+// b_v = (1/n_v) sum_j C_jv r_j
+__global__ void back_f64_kernel(const uint32_t *col_ptr, const uint32_t *row, const uint32_t *cnt,
+                                const uint32_t *n_v, const double *r, int64_t n, double *b) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) acc += (double)cnt[k] * r[row[k]];
+    b[v] = n_v[v] ? acc / (double)n_v[v] : 0.0;
+  }
+}
+
+// Quadratic 6-neighbour prior R(x) = beta/2 sum over neighbour pairs (x_v - x_w)^2
+// (each pair once); grad_v = beta sum over the neighbours w of v (x_v - x_w).
+template <typename T>
+__global__ void prior_kernel(int nx, int ny, int nz, double beta, const T *x, T *grad, double *partials) {
+  __shared__ double s_tmp[32];
+  const int64_t n = (int64_t)nx * ny * nz;
+  double val = 0.0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+    const double xv = (double)x[v];
+    double g = 0.0;
+    if (i > 0) g += xv - (double)x[v - 1];
+    if (i < nx - 1) { const double d = xv - (double)x[v + 1]; g += d; val += d * d; }
+    if (j > 0) g += xv - (double)x[v - nx];
+    if (j < ny - 1) { const double d = xv - (double)x[v + nx]; g += d; val += d * d; }
+    if (k > 0) g += xv - (double)x[v - (int64_t)nx * ny];
+    if (k < nz - 1) { const double d = xv - (double)x[v + (int64_t)nx * ny]; g += d; val += d * d; }
+    if (grad) grad[v] = (T)(beta * g);
+  }
+  if (partials) {
+    const double t = block_sum_double(0.5 * beta * val, s_tmp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+// x_v <- max(0, x_v - alpha (x_v / s_v) (s_v - bp_v + gp_v)): gradient descent on
+// sum_j (q_j - y_j ln q_j) + R(x) with the EM preconditioner x / s; alpha = 1
+// and no prior is one ML-EM update.  Voxels with s_v = 0 are set to 0.
+__global__ void pgd_step_kernel(int64_t n, double alpha, const double *sens, const float *bp, const float *gp,
+                                float *x) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const double s = sens[v];
+    if (!(s > 0.0)) { x[v] = 0.0f; continue; }
+    const double grad = s - (double)bp[v] + (gp ? (double)gp[v] : 0.0);
+    const double xn = (double)x[v] - alpha * ((double)x[v] / s) * grad;
+    x[v] = (float)(xn > 0.0 ? xn : 0.0);
+  }
+}
+
+int project_f64(const mc_system *sys, const double *x, double *q, cudaStream_t s) {
+  if (sys->n_rows > 0) {
+    count_launch();
+    forward_f64_kernel<<<grid_stride_blocks(sys->n_rows), 256, 0, s>>>(
+        sys->row_ptr.as<uint32_t>(), sys->col_idx.as<uint32_t>(), sys->csr_cnt.as<uint32_t>(),
+        sys->n_v.as<uint32_t>(), x, sys->n_rows, q);
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+int backproject_f64(const mc_system *sys, const double *r, double *b, cudaStream_t s) {
+  if (sys->n_cols > 0) {
+    count_launch();
+    back_f64_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(
+        sys->col_ptr.as<uint32_t>(), sys->row_idx.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
+        sys->n_v.as<uint32_t>(), r, sys->n_cols, b);
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+template <typename T>
+int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, double *value, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int nb = grid_stride_blocks(n);
+  DevBuf part;
+  if (value) MCS_TRY(part.alloc((size_t)nb * sizeof(double), s));
+  count_launch();
+  prior_kernel<T><<<nb, 256, 0, s>>>(nx, ny, nz, beta, x, grad, value ? part.as<double>() : nullptr);
+  MCS_LAUNCHED();
+  if (value) {
+    count_launch();
+    sum_partials_kernel<<<1, 1024, 0, s>>>(part.as<double>(), nb, value);
+    MCS_LAUNCHED();
+  }
+  return MC_OK;
+}
+template int prior_quadratic<float>(int, int, int, double, const float *, float *, double *, cudaStream_t);
+template int prior_quadratic<double>(int, int, int, double, const double *, double *, double *, cudaStream_t);
+
+int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const float *gp, float *x, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    pgd_step_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(n, alpha, sens, bp, gp, x);
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+}  // namespace mcs

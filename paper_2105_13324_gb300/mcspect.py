@@ -31,7 +31,8 @@ EXPORTED = (
     "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
-    "mc_system_subset", "osem_iterate",
+    "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
+    "mc_prior_quadratic_f64", "mc_pgd_step",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
 )
 
@@ -108,6 +109,12 @@ def load(path: str | None = None):
             "mlem_iterate_noalloc": [vp, vp, vp, i32, vp, vp],
             "mc_system_subset": [vp, i64, i32, i32, vp, vp],
             "osem_iterate": [vp, vp, i32, vp, vp, vp, i32, vp],
+            "mc_project_ratio": [vp, vp, vp, vp, vp],
+            "mc_project_f64": [vp, vp, vp, vp],
+            "mc_backproject_f64": [vp, vp, vp, vp],
+            "mc_prior_quadratic": [i32, i32, i32, dbl, vp, vp, vp, vp],
+            "mc_prior_quadratic_f64": [i32, i32, i32, dbl, vp, vp, vp, vp],
+            "mc_pgd_step": [i64, dbl, vp, vp, vp, vp, vp],
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
             "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
@@ -374,6 +381,46 @@ def osem_iterate(fwd, back, y, x, n_iter: int, add=None, stream=None):
     _check(load().osem_iterate(arr, brr, len(fwd), _dev_ptr(y, torch.float32),
                                _dev_ptr(add, torch.float32) if add is not None else None,
                                _dev_ptr(x, torch.float32), int(n_iter), _stream_ptr(stream)))
+    return x
+
+
+def mc_project_ratio(sys: System, x, y, r, stream=None):
+    import torch
+    _check(load().mc_project_ratio(sys.handle, _dev_ptr(x, torch.float32), _dev_ptr(y, torch.float32),
+                                   _dev_ptr(r, torch.float32), _stream_ptr(stream)))
+    return r
+
+
+def mc_project_f64(sys: System, x, q, stream=None):
+    import torch
+    _check(load().mc_project_f64(sys.handle, _dev_ptr(x, torch.float64), _dev_ptr(q, torch.float64),
+                                 _stream_ptr(stream)))
+    return q
+
+
+def mc_backproject_f64(sys: System, r, b, stream=None):
+    import torch
+    _check(load().mc_backproject_f64(sys.handle, _dev_ptr(r, torch.float64), _dev_ptr(b, torch.float64),
+                                     _stream_ptr(stream)))
+    return b
+
+
+def mc_prior_quadratic(shape, beta: float, x, grad=None, value=None, stream=None):
+    """Quadratic 6-neighbour prior of an image of shape (nz, ny, nx)."""
+    import torch
+    nz, ny, nx = shape
+    f = load().mc_prior_quadratic if x.dtype == torch.float32 else load().mc_prior_quadratic_f64
+    _check(f(int(nx), int(ny), int(nz), float(beta), _dev_ptr(x, x.dtype),
+             _dev_ptr(grad, x.dtype) if grad is not None else None,
+             _dev_ptr(value, torch.float64) if value is not None else None, _stream_ptr(stream)))
+    return grad, value
+
+
+def mc_pgd_step(alpha: float, sens, bp, x, gp=None, stream=None):
+    import torch
+    _check(load().mc_pgd_step(int(x.numel()), float(alpha), _dev_ptr(sens, torch.float64),
+                              _dev_ptr(bp, torch.float32), _dev_ptr(gp, torch.float32) if gp is not None else None,
+                              _dev_ptr(x, torch.float32), _stream_ptr(stream)))
     return x
 
 
