@@ -194,6 +194,11 @@ MC_API int mc_project(const mc_system *sys, const float *x_dev, float *q_dev, vo
  * the other projector calls on one system. */
 MC_API int mc_project_ratio(const mc_system *sys, const float *x_dev, const float *y_dev, float *r_dev, void *stream);
 
+/* Poisson log-likelihood of Sec. 5.1 (up to a constant) of an image:
+ * *value_dev = sum_j y_j ln q_j - q_j, q = A x, bins with y_j = 0 adding
+ * -q_j; FP64 accumulation.  x_dev[N], y_dev[M] float; value_dev one double. */
+MC_API int mc_loglik(const mc_system *sys, const float *x_dev, const float *y_dev, double *value_dev, void *stream);
+
 /* Back-projection b = A^T r: r_dev[M], b_dev[N], float. */
 MC_API int mc_backproject(const mc_system *sys, const float *r_dev, float *b_dev, void *stream);
 

@@ -73,8 +73,13 @@ def penalised_objective(x, system, y, shape, beta):
     return q.sum() - (y[pos] * torch.log(q[pos])).sum() + quadratic_prior(x, shape, beta)
 
 
-def penalised_reconstruct(system, y, shape, beta: float, n_iter: int, alpha: float = 1.0, x0=None):
-    """EM-preconditioned projected gradient descent on Φ (float32)."""
+def penalised_reconstruct(system, y, shape, beta: float, n_iter: int, alpha: float = 1.0, x0=None,
+                          history: list | None = None):
+    """EM-preconditioned projected gradient descent on Φ (float32 images,
+    FP64 objective).  Each step starts at `alpha` and halves it until Φ does
+    not increase (at most 20 halvings), so Φ decreases monotonically; with
+    β = 0 and alpha = 1 the first trial is the ML-EM update, which never
+    increases Φ.  `history` (a list) receives Φ after each step."""
     m, n = system.shape
     dev = y.device
     sens = torch.empty(n, dtype=torch.float64, device=dev)
@@ -87,10 +92,33 @@ def penalised_reconstruct(system, y, shape, beta: float, n_iter: int, alpha: flo
     r = torch.empty(m, dtype=torch.float32, device=dev)
     bp = torch.empty(n, dtype=torch.float32, device=dev)
     gp = torch.empty(n, dtype=torch.float32, device=dev) if beta > 0 else None
+    ll = torch.zeros(1, dtype=torch.float64, device=dev)
+    pv = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def phi(img):
+        mc.mc_loglik(system, img, y, ll)
+        val = -float(ll.item())
+        if beta > 0:
+            mc.mc_prior_quadratic(shape, beta, img, None, pv)
+            val += float(pv.item())
+        return val
+
+    cur = phi(x)
     for _ in range(n_iter):
         mc.mc_project_ratio(system, x, y, r)
         mc.mc_backproject(system, r, bp)
         if gp is not None:
             mc.mc_prior_quadratic(shape, beta, x, gp)
-        mc.mc_pgd_step(alpha, sens, bp, x, gp)
+        a = alpha
+        for _ in range(21):
+            xn = x.clone()
+            mc.mc_pgd_step(a, sens, bp, xn, gp)
+            new = phi(xn)
+            if new <= cur or a < alpha * 2.0 ** -19:
+                break
+            a *= 0.5
+        if new <= cur:
+            x, cur = xn, new
+        if history is not None:
+            history.append(cur)
     return x

@@ -66,6 +66,7 @@ int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const flo
 int forward_blocks(const mc_system *sys);
 int project_f64(const mc_system *sys, const double *x, double *q, cudaStream_t s);
 int project_ratio(const mc_system *sys, const float *x, const float *y, float *r, cudaStream_t s);
+int loglik(const mc_system *sys, const float *x, const float *y, double *value, cudaStream_t s);
 int backproject_f64(const mc_system *sys, const double *r, double *b, cudaStream_t s);
 template <typename T>
 int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, double *value, cudaStream_t s);
@@ -641,6 +642,12 @@ int mc_project_ratio(const mc_system *sys, const float *x_dev, const float *y_de
   clear_error();
   if (!sys || !x_dev || !y_dev || !r_dev) { set_error("NULL argument"); return MC_EINVAL; }
   return project_ratio(sys, x_dev, y_dev, r_dev, API_STREAM(stream));
+}
+
+int mc_loglik(const mc_system *sys, const float *x_dev, const float *y_dev, double *value_dev, void *stream) {
+  clear_error();
+  if (!sys || !x_dev || !y_dev || !value_dev) { set_error("NULL argument"); return MC_EINVAL; }
+  return loglik(sys, x_dev, y_dev, value_dev, API_STREAM(stream));
 }
 
 int mc_project_f64(const mc_system *sys, const double *x_dev, double *q_dev, void *stream) {

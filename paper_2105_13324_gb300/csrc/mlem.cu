@@ -537,6 +537,24 @@ int project_ratio(const mc_system *sys, const float *x, const float *y, float *r
   return MC_OK;
 }
 
+// L(x) = sum_j y_j ln q_j - q_j (FP64), q = A x, into *value (device)
+int loglik(const mc_system *sys, const float *x, const float *y, double *value, cudaStream_t s) {
+  if (sys->n_cols > 0) {
+    count_launch();
+    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
+                                                                     sys->n_cols);
+  }
+  if (sys->n_rows > 0) {
+    fwd_dispatch<1, true>(sys, sys->xs.as<float>(), y, sys->r.as<float>(), sys->partials.as<double>(), s);
+    count_launch();
+    sum_partials_kernel<<<1, 1024, 0, s>>>(sys->partials.as<double>(), forward_blocks(sys), value);
+  } else {
+    MCS_CUDA(cudaMemsetAsync(value, 0, sizeof(double), s));
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
 int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s) {
   if (sys->n_cols > 0) back_dispatch<0>(sys, r, b, nullptr, s);
   MCS_LAUNCHED();

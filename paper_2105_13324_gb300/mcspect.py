@@ -31,7 +31,7 @@ EXPORTED = (
     "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
-    "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
+    "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
     "mc_prior_quadratic_f64", "mc_pgd_step",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
 )
@@ -110,6 +110,7 @@ def load(path: str | None = None):
             "mc_system_subset": [vp, i64, i32, i32, vp, vp],
             "osem_iterate": [vp, vp, i32, vp, vp, vp, i32, vp],
             "mc_project_ratio": [vp, vp, vp, vp, vp],
+            "mc_loglik": [vp, vp, vp, vp, vp],
             "mc_project_f64": [vp, vp, vp, vp],
             "mc_backproject_f64": [vp, vp, vp, vp],
             "mc_prior_quadratic": [i32, i32, i32, dbl, vp, vp, vp, vp],
@@ -389,6 +390,13 @@ def mc_project_ratio(sys: System, x, y, r, stream=None):
     _check(load().mc_project_ratio(sys.handle, _dev_ptr(x, torch.float32), _dev_ptr(y, torch.float32),
                                    _dev_ptr(r, torch.float32), _stream_ptr(stream)))
     return r
+
+
+def mc_loglik(sys: System, x, y, value, stream=None):
+    import torch
+    _check(load().mc_loglik(sys.handle, _dev_ptr(x, torch.float32), _dev_ptr(y, torch.float32),
+                            _dev_ptr(value, torch.float64), _stream_ptr(stream)))
+    return value
 
 
 def mc_project_f64(sys: System, x, q, stream=None):
