@@ -115,6 +115,8 @@ typedef struct mc_system_info {
   double build_ms_transport; /* device time of the build's transport kernel */
   double build_ms_assembly;  /* ... of matrix assembly (sort, CSR/CSC, sums) */
   double build_ms_detect;    /* ... of the collimator/detector kernel */
+  int32_t spmv_fwd, spmv_bwd; /* projector kernels: 0 = streaming tiles,
+                                 else lanes per row (column) group */
 } mc_system_info;
 
 /* Per-history trace (verification): 48 bytes, this exact layout. */
@@ -270,6 +272,27 @@ MC_API int mc_prior_quadratic_f64(int32_t nx, int32_t ny, int32_t nz, double bet
  * prior is one ML-EM update (Eq. (MLEM)). */
 MC_API int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp_dev, const float *gp_dev,
                        float *x_dev, void *stream);
+
+/* SpMV autotuner: times the forward and back-projection kernels of `sys`
+ * (streaming tiles, row groups of 1..32 lanes) on its own matrix and keeps
+ * the fastest of each (reported by mc_system_info_get).  Synchronises. */
+MC_API int mc_system_autotune(mc_system *sys, void *stream);
+
+/* Batched ML-EM (serving many acquisitions): n systems with their
+ * projections y_dev[k] (rows of system k) and images x_dev[k] (columns of
+ * system k), all device memory owned by the caller and kept alive while the
+ * batch exists.  mc_batch_mlem sets every image to its uniform start
+ * (mc_mlem_init) and runs n_iter updates of Eq. (MLEM) for all of them: one
+ * forward and one back-projection launch per iteration over all systems,
+ * captured once into a CUDA graph per n_iter and replayed.  Every system
+ * must be a full FP32 system with streaming tiles (short rows, as MC
+ * matrices of moderate history counts have); results equal mlem_iterate's.
+ * Systems in a batch must not be used by other calls while it runs. */
+typedef struct mc_batch mc_batch;
+MC_API int mc_batch_create(mc_system *const *systems, int32_t n, const float *const *y_dev, float *const *x_dev,
+                           mc_batch **out);
+MC_API int mc_batch_mlem(mc_batch *batch, int32_t n_iter, void *stream);
+MC_API int mc_batch_free(mc_batch *batch);
 
 /* ML-EM like mlem_iterate, for callers that must not allocate device
  * memory: a reconstruction service that plans its memory up front (a device

@@ -71,6 +71,9 @@ int backproject_f64(const mc_system *sys, const double *r, double *b, cudaStream
 template <typename T>
 int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, double *value, cudaStream_t s);
 int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const float *gp, float *x, cudaStream_t s);
+int batch_create(mc_system *const *sys, int n, const float *const *y, float *const *x, mc_batch **out);
+int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s);
+int autotune(mc_system *sys, cudaStream_t s, int *fwd_choice, int *bwd_choice);
 void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
                           std::vector<float> &sig_tab);
 
@@ -487,6 +490,8 @@ int mc_system_info_get(const mc_system *sys, mc_system_info *info) {
   info->build_ms_transport = sys->ms_transport;
   info->build_ms_assembly = sys->ms_assembly;
   info->build_ms_detect = sys->ms_detect;
+  info->spmv_fwd = sys->n_csr_blocks > 0 ? 0 : sys->spmv_group_fwd;
+  info->spmv_bwd = sys->n_csc_blocks > 0 ? 0 : sys->spmv_group_bwd;
   return MC_OK;
 }
 
@@ -689,6 +694,33 @@ int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp
   if (!sens_dev || !bp_dev || !x_dev || n < 0) { set_error("NULL argument or negative size"); return MC_EINVAL; }
   if (!(alpha > 0.0) || !std::isfinite(alpha)) { set_error("alpha must be positive"); return MC_EINVAL; }
   return pgd_step(n, alpha, sens_dev, bp_dev, gp_dev, x_dev, API_STREAM(stream));
+}
+
+int mc_system_autotune(mc_system *sys, void *stream) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  int f = 0, b = 0;
+  return autotune(sys, API_STREAM(stream), &f, &b);
+}
+
+int mc_batch_create(mc_system *const *systems, int32_t n, const float *const *y_dev, float *const *x_dev,
+                    mc_batch **out) {
+  clear_error();
+  if (!systems || !y_dev || !x_dev || !out || n < 1) { set_error("NULL argument or empty batch"); return MC_EINVAL; }
+  *out = nullptr;
+  return batch_create(systems, n, y_dev, x_dev, out);
+}
+
+int mc_batch_mlem(mc_batch *batch, int32_t n_iter, void *stream) {
+  clear_error();
+  if (!batch || n_iter < 0) { set_error("NULL batch or negative n_iter"); return MC_EINVAL; }
+  return batch_mlem(batch, n_iter, API_STREAM(stream));
+}
+
+int mc_batch_free(mc_batch *batch) {
+  clear_error();
+  delete batch;
+  return MC_OK;
 }
 
 int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, uint64_t seed, uint64_t first,

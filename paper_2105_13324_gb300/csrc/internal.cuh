@@ -123,6 +123,8 @@ struct mc_system {
   int32_t n_subsets = 1, subset = 0;
 };
 
+struct mc_batch;
+
 namespace mcs {
 
 // ---------------------------------------------------------------------------

@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -855,6 +857,275 @@ int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const
     pgd_step_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(n, alpha, sens, bp, gp, x);
   }
   MCS_LAUNCHED();
+  return MC_OK;
+}
+
+}  // namespace mcs
+
+// ---------------------------------------------------------------------------
+// batched ML-EM over many systems (serving many acquisitions at once)
+// ---------------------------------------------------------------------------
+// Each iteration is one forward launch over the concatenated CSR tiles of
+// all systems and one back-projection launch over their CSC tiles; a block
+// finds its system by binary search in the prefix of tile counts.  The
+// whole reconstruction (start images + n_iter iterations) is captured once
+// in a CUDA graph and replayed.
+namespace mcs {
+
+struct BatchSys {
+  const uint32_t *row_ptr, *csr_tiles, *col_idx, *col_ptr, *csc_tiles, *row_idx;
+  const float *csr_val, *csc_val, *inv_n, *inv_colsum, *y;
+  const double *colsum;
+  const uint32_t *n_v;
+  float *x, *xs, *r;
+  int64_t n_rows, n_cols;
+  int warp_fwd, warp_bwd;
+};
+
+__device__ __forceinline__ int batch_find(const uint64_t *off, int n, uint64_t i) {
+  int lo = 0, hi = n - 1;  // largest k with off[k] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
+                                                                    const uint64_t *__restrict__ tile_off,
+                                                                    int n_sys) {
+  __shared__ float s_prod[kStreamTile];
+  const int k = batch_find(tile_off, n_sys, blockIdx.x);
+  const BatchSys &S = systems[k];
+  const uint32_t tile = (uint32_t)(blockIdx.x - tile_off[k]);
+  const uint32_t r0 = S.csr_tiles[tile], r1 = S.csr_tiles[tile + 1];
+  const uint32_t p0 = S.row_ptr[r0];
+  stream_products<float>(p0, S.row_ptr[r1] - p0, S.col_idx, S.csr_val, S.xs, s_prod);
+  __syncthreads();
+  if (S.warp_fwd) {
+    for (uint32_t r = r0 + (threadIdx.x >> 5); r < r1; r += kStreamThreads / 32) {
+      const float acc = stream_segment<true>(s_prod, S.row_ptr[r] - p0, S.row_ptr[r + 1] - p0);
+      if ((threadIdx.x & 31) == 0) S.r[r] = acc > 0.0f ? S.y[r] / acc : 0.0f;
+    }
+  } else {
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += kStreamThreads) {
+      const float acc = stream_segment<false>(s_prod, S.row_ptr[r] - p0, S.row_ptr[r + 1] - p0);
+      S.r[r] = acc > 0.0f ? S.y[r] / acc : 0.0f;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchSys *__restrict__ systems,
+                                                                 const uint64_t *__restrict__ tile_off, int n_sys) {
+  __shared__ float s_prod[kStreamTile];
+  const int k = batch_find(tile_off, n_sys, blockIdx.x);
+  const BatchSys &S = systems[k];
+  const uint32_t tile = (uint32_t)(blockIdx.x - tile_off[k]);
+  const uint32_t c0 = S.csc_tiles[tile], c1 = S.csc_tiles[tile + 1];
+  const uint32_t p0 = S.col_ptr[c0];
+  stream_products<float>(p0, S.col_ptr[c1] - p0, S.row_idx, S.csc_val, S.r, s_prod);
+  __syncthreads();
+  const bool warp = S.warp_bwd != 0;
+  const uint32_t first = warp ? (threadIdx.x >> 5) : threadIdx.x;
+  const uint32_t step = warp ? kStreamThreads / 32 : kStreamThreads;
+  for (uint32_t v = c0 + first; v < c1; v += step) {
+    const float acc = warp ? stream_segment<true>(s_prod, S.col_ptr[v] - p0, S.col_ptr[v + 1] - p0)
+                           : stream_segment<false>(s_prod, S.col_ptr[v] - p0, S.col_ptr[v + 1] - p0);
+    if (!warp || (threadIdx.x & 31) == 0) {
+      const float is = S.inv_colsum[v];
+      const float xn = is > 0.0f ? S.x[v] * acc * is : 0.0f;
+      S.x[v] = xn;
+      S.xs[v] = xn * S.inv_n[v];
+    }
+  }
+}
+
+// start images: block k computes x0_k = sum(y_k) / sum(s_k)
+__global__ void batch_init_sums_kernel(const BatchSys *systems, double *x0) {
+  __shared__ double s_tmp[32];
+  const BatchSys &S = systems[blockIdx.x];
+  double ay = 0.0, as = 0.0;
+  for (int64_t i = threadIdx.x; i < S.n_rows; i += blockDim.x) ay += (double)S.y[i];
+  for (int64_t v = threadIdx.x; v < S.n_cols; v += blockDim.x)
+    if (S.n_v[v]) as += S.colsum[v] / (double)S.n_v[v];
+  const double ty = block_sum_double(ay, s_tmp);
+  const double ts = block_sum_double(as, s_tmp);
+  if (threadIdx.x == 0) x0[blockIdx.x] = ts > 0.0 ? ty / ts : 0.0;
+}
+
+__global__ void batch_init_fill_kernel(const BatchSys *systems, const uint64_t *vox_off, int n_sys, uint64_t total,
+                                       const double *x0) {
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+    const int k = batch_find(vox_off, n_sys, g);
+    const BatchSys &S = systems[k];
+    const uint64_t v = g - vox_off[k];
+    const float xv = S.colsum[v] > 0.0 ? (float)x0[k] : 0.0f;
+    S.x[v] = xv;
+    S.xs[v] = xv * S.inv_n[v];
+  }
+}
+
+}  // namespace mcs
+
+struct mc_batch {
+  int n = 0;
+  mcs::DevBuf systems, tile_fwd, tile_bwd, vox_off, x0;
+  uint64_t n_tiles_fwd = 0, n_tiles_bwd = 0, n_vox = 0;
+  cudaGraphExec_t exec = nullptr;
+  int exec_iters = -1;
+  ~mc_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+namespace mcs {
+
+int batch_create(mc_system *const *sys, int n, const float *const *y, float *const *x, mc_batch **out) {
+  std::vector<BatchSys> hs(n);
+  std::vector<uint64_t> tf(n + 1, 0), tb(n + 1, 0), vo(n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    const mc_system *s = sys[k];
+    if (!s || !y[k] || !x[k]) { set_error("batch entry %d: NULL system or vector", k); return MC_EINVAL; }
+    if (s->n_csr_blocks <= 0 || s->n_csc_blocks <= 0 || s->value_type != MC_VAL_F32 || s->row_map.p) {
+      set_error("batch entry %d: needs a full FP32 system with streaming tiles (short rows)", k);
+      return MC_EINVAL;
+    }
+    BatchSys &b = hs[k];
+    b.row_ptr = s->row_ptr.as<uint32_t>(); b.csr_tiles = s->csr_blocks.as<uint32_t>(); b.col_idx = s->col_idx.as<uint32_t>();
+    b.col_ptr = s->col_ptr.as<uint32_t>(); b.csc_tiles = s->csc_blocks.as<uint32_t>(); b.row_idx = s->row_idx.as<uint32_t>();
+    b.csr_val = s->csr_val.as<float>(); b.csc_val = s->csc_val.as<float>();
+    b.inv_n = s->inv_n.as<float>(); b.inv_colsum = s->inv_colsum.as<float>(); b.y = y[k];
+    b.colsum = s->colsum.as<double>(); b.n_v = s->n_v.as<uint32_t>();
+    b.x = x[k]; b.xs = s->xs.as<float>(); b.r = s->r.as<float>();
+    b.n_rows = s->n_rows; b.n_cols = s->n_cols;
+    b.warp_fwd = s->warp_rows_fwd; b.warp_bwd = s->warp_rows_bwd;
+    tf[k + 1] = tf[k] + (uint64_t)s->n_csr_blocks;
+    tb[k + 1] = tb[k] + (uint64_t)s->n_csc_blocks;
+    vo[k + 1] = vo[k] + (uint64_t)s->n_cols;
+  }
+  if (tf[n] >= (1ull << 31) || tb[n] >= (1ull << 31)) { set_error("too many tiles for one launch"); return MC_EINVAL; }
+  mc_batch *b = new (std::nothrow) mc_batch();
+  if (!b) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete b; return rc; };
+  cudaStream_t s = nullptr;
+  int rc;
+  if ((rc = b->systems.alloc(n * sizeof(BatchSys), s)) || (rc = b->tile_fwd.alloc((n + 1) * 8, s)) ||
+      (rc = b->tile_bwd.alloc((n + 1) * 8, s)) || (rc = b->vox_off.alloc((n + 1) * 8, s)) ||
+      (rc = b->x0.alloc(n * sizeof(double), s)))
+    return fail(rc);
+  if (cudaMemcpyAsync(b->systems.p, hs.data(), n * sizeof(BatchSys), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->tile_fwd.p, tf.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->tile_bwd.p, tb.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b->vox_off.p, vo.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("batch upload failed");
+    return fail(MC_ECUDA);
+  }
+  b->n = n;
+  b->n_tiles_fwd = tf[n];
+  b->n_tiles_bwd = tb[n];
+  b->n_vox = vo[n];
+  *out = b;
+  return MC_OK;
+}
+
+// Enqueue the whole batched reconstruction on s (used once for capture).
+static int batch_enqueue(mc_batch *b, int n_iter, cudaStream_t s) {
+  const BatchSys *sys = b->systems.as<BatchSys>();
+  count_launch();
+  batch_init_sums_kernel<<<b->n, 1024, 0, s>>>(sys, b->x0.as<double>());
+  count_launch();
+  batch_init_fill_kernel<<<grid_stride_blocks((int64_t)b->n_vox), 256, 0, s>>>(sys, b->vox_off.as<uint64_t>(), b->n,
+                                                                               b->n_vox, b->x0.as<double>());
+  for (int it = 0; it < n_iter; ++it) {
+    if (b->n_tiles_fwd) {
+      count_launch();
+      batch_forward_kernel<<<(unsigned)b->n_tiles_fwd, kStreamThreads, 0, s>>>(sys, b->tile_fwd.as<uint64_t>(), b->n);
+    }
+    if (b->n_tiles_bwd) {
+      count_launch();
+      batch_back_kernel<<<(unsigned)b->n_tiles_bwd, kStreamThreads, 0, s>>>(sys, b->tile_bwd.as<uint64_t>(), b->n);
+    }
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s) {
+  if (!b->exec || b->exec_iters != n_iter) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    cudaStream_t cap = nullptr;
+    MCS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = MC_OK;
+    if (e == cudaSuccess) {
+      rc = batch_enqueue(b, n_iter, cap);
+      e = cudaStreamEndCapture(cap, &g);
+    }
+    if (e == cudaSuccess && rc == MC_OK) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc != MC_OK) return rc;
+    if (e != cudaSuccess) { set_error("batch graph capture failed: %s", cudaGetErrorString(e)); return MC_ECUDA; }
+    b->exec_iters = n_iter;
+  }
+  MCS_CUDA(cudaGraphLaunch(b->exec, s));
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SpMV autotuner: per system, the fastest of the streaming tiles and the row
+// groups of 1..32 lanes, for the forward and the back-projection separately
+// ---------------------------------------------------------------------------
+int autotune(mc_system *sys, cudaStream_t s, int *fwd_choice, int *bwd_choice) {
+  if (sys->n_rows == 0 || sys->n_cols == 0 || sys->nnz == 0) { *fwd_choice = *bwd_choice = -1; return MC_OK; }
+  cudaEvent_t a = nullptr, b = nullptr;
+  MCS_CUDA(cudaEventCreate(&a));
+  MCS_CUDA(cudaEventCreate(&b));
+  const int64_t fwd_tiles = sys->n_csr_blocks, bwd_tiles = sys->n_csc_blocks;
+  const int g_fwd0 = sys->spmv_group_fwd, g_bwd0 = sys->spmv_group_bwd;
+  float best_f = 1e30f, best_b = 1e30f;
+  int choice_f = -1, choice_b = -1;
+  const int groups[6] = {1, 2, 4, 8, 16, 32};
+  for (int c = -1; c < 6; ++c) {  // -1: streaming tiles
+    if (c == -1 && fwd_tiles == 0 && bwd_tiles == 0) continue;
+    sys->n_csr_blocks = c == -1 ? fwd_tiles : 0;
+    sys->n_csc_blocks = c == -1 ? bwd_tiles : 0;
+    if (c >= 0) { sys->spmv_group_fwd = groups[c]; sys->spmv_group_bwd = groups[c]; }
+    for (int pass = 0; pass < 2; ++pass) {  // warm-up, then timed
+      float tf = 0.f, tb = 0.f;
+      if (c >= 0 || fwd_tiles) {
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 5; ++r) fwd_dispatch<0, false>(sys, sys->xs.as<float>(), nullptr, sys->r.as<float>(), nullptr, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&tf, a, b);
+        if (pass && tf < best_f) { best_f = tf; choice_f = c; }
+      }
+      if (c >= 0 || bwd_tiles) {
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 5; ++r) back_dispatch<0>(sys, sys->r.as<float>(), sys->xs.as<float>(), nullptr, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&tb, a, b);
+        if (pass && tb < best_b) { best_b = tb; choice_b = c; }
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  MCS_LAUNCHED();
+  sys->n_csr_blocks = choice_f == -1 ? fwd_tiles : 0;
+  sys->n_csc_blocks = choice_b == -1 ? bwd_tiles : 0;
+  sys->spmv_group_fwd = choice_f >= 0 ? groups[choice_f] : g_fwd0;
+  sys->spmv_group_bwd = choice_b >= 0 ? groups[choice_b] : g_bwd0;
+  // partials must cover the forward blocks of the chosen kernel
+  const int fb = forward_blocks(sys);
+  if ((size_t)fb * sizeof(double) > sys->partials.bytes) MCS_TRY(sys->partials.alloc((size_t)fb * sizeof(double), s));
+  *fwd_choice = choice_f == -1 ? 0 : groups[choice_f];
+  *bwd_choice = choice_b == -1 ? 0 : groups[choice_b];
+  MCS_CUDA(cudaStreamSynchronize(s));
   return MC_OK;
 }
 

@@ -32,7 +32,8 @@ EXPORTED = (
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
     "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
-    "mc_prior_quadratic_f64", "mc_pgd_step",
+    "mc_prior_quadratic_f64", "mc_pgd_step", "mc_system_autotune", "mc_batch_create", "mc_batch_mlem",
+    "mc_batch_free",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
 )
 
@@ -71,7 +72,8 @@ class MCSystemInfo(ctypes.Structure):
                 ("n_events", ctypes.c_int64), ("first_history", ctypes.c_uint64),
                 ("n_histories", ctypes.c_uint64), ("fates", ctypes.c_uint64 * 4), ("max_count", ctypes.c_uint32),
                 ("value_type", ctypes.c_int32), ("build_ms_transport", ctypes.c_double),
-                ("build_ms_assembly", ctypes.c_double), ("build_ms_detect", ctypes.c_double)]
+                ("build_ms_assembly", ctypes.c_double), ("build_ms_detect", ctypes.c_double),
+                ("spmv_fwd", ctypes.c_int32), ("spmv_bwd", ctypes.c_int32)]
 
 
 _lib = None
@@ -116,6 +118,10 @@ def load(path: str | None = None):
             "mc_prior_quadratic": [i32, i32, i32, dbl, vp, vp, vp, vp],
             "mc_prior_quadratic_f64": [i32, i32, i32, dbl, vp, vp, vp, vp],
             "mc_pgd_step": [i64, dbl, vp, vp, vp, vp, vp],
+            "mc_system_autotune": [vp, vp],
+            "mc_batch_create": [vp, i32, vp, vp, vp],
+            "mc_batch_mlem": [vp, i32, vp],
+            "mc_batch_free": [vp],
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
             "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
@@ -199,7 +205,8 @@ class System:
                 "first_history": inf.first_history, "n_histories": inf.n_histories,
                 "fates": [int(v) for v in inf.fates], "max_count": inf.max_count,
                 "value_type": inf.value_type, "build_ms_transport": inf.build_ms_transport,
-                "build_ms_assembly": inf.build_ms_assembly, "build_ms_detect": inf.build_ms_detect}
+                "build_ms_assembly": inf.build_ms_assembly, "build_ms_detect": inf.build_ms_detect,
+                "spmv_fwd": inf.spmv_fwd, "spmv_bwd": inf.spmv_bwd}
 
     @property
     def shape(self):
@@ -430,6 +437,57 @@ def mc_pgd_step(alpha: float, sens, bp, x, gp=None, stream=None):
                               _dev_ptr(bp, torch.float32), _dev_ptr(gp, torch.float32) if gp is not None else None,
                               _dev_ptr(x, torch.float32), _stream_ptr(stream)))
     return x
+
+
+def mc_system_autotune(sys: System, stream=None):
+    _check(load().mc_system_autotune(sys.handle, _stream_ptr(stream)))
+    i = sys.info()
+    return i["spmv_fwd"], i["spmv_bwd"]
+
+
+class Batch:
+    """Batched ML-EM of many systems (mc_batch); keeps its tensors alive."""
+
+    def __init__(self, systems, ys, xs):
+        import torch
+        if not (len(systems) == len(ys) == len(xs)) or not systems:
+            raise ValueError("need the same, non-zero number of systems, projections and images")
+        self._keep = (list(systems), list(ys), list(xs))
+        n = len(systems)
+        sarr = (ctypes.c_void_p * n)(*[s.handle for s in systems])
+        yarr = (ctypes.c_void_p * n)(*[_dev_ptr(y, torch.float32).value for y in ys])
+        xarr = (ctypes.c_void_p * n)(*[_dev_ptr(x, torch.float32).value for x in xs])
+        h = ctypes.c_void_p()
+        _check(load().mc_batch_create(sarr, n, yarr, xarr, ctypes.byref(h)))
+        self._h = h
+
+    def mlem(self, n_iter: int, stream=None):
+        _check(load().mc_batch_mlem(self._h, int(n_iter), _stream_ptr(stream)))
+
+    def free(self):
+        if self._h:
+            _check(load().mc_batch_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.mc_batch_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def mc_batch_create(systems, ys, xs) -> Batch:
+    return Batch(systems, ys, xs)
+
+
+def mc_batch_mlem(batch: Batch, n_iter: int, stream=None):
+    batch.mlem(n_iter, stream)
+
+
+def mc_batch_free(batch: Batch):
+    batch.free()
 
 
 def mc_trace_histories(phantom, geometry, seed: int, first: int, count: int, precision="fp64",
