@@ -273,6 +273,59 @@ def roof_instance(mc, plan, histories, seed, n_iter, flush, stream, hbm_gbs, pea
     return out
 
 
+def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
+    """Mixed-size serving batch: n_phantoms torso acquisitions (48^3..128^3,
+    40-120 views), each with its own system (`histories` histories) and
+    Poisson projections; reconstructed together by the batched graph, and
+    one by one (autotuned kernels) for the per-phantom latency."""
+    import torch
+    mix = P.serving_mix(n_phantoms, seed=5)
+    systems, ys = [], []
+    t0 = time.perf_counter()
+    for ph, g, counts, seed in mix:
+        s = mc.mc_build_system(ph, g, histories, seed)
+        q = torch.zeros(s.shape[0], dtype=torch.float32, device="cuda")
+        mc.mc_project(s, torch.as_tensor(ph.activity.ravel()).cuda(), q)
+        ys.append(torch.as_tensor(P.poisson_counts(q.cpu().numpy(), counts, seed)).cuda())
+        systems.append(s)
+    build_s = time.perf_counter() - t0
+    xs = [torch.zeros(s.shape[1], dtype=torch.float32, device="cuda") for s in systems]
+    batch = mc.Batch(systems, ys, xs)
+    batch.mlem(n_iter, stream)                 # capture + warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(5):
+        e0.record(stream)
+        batch.mlem(n_iter, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    batch_ms = float(np.median(ms))
+    lat = []
+    for s, y, x in zip(systems, ys, xs):
+        mc.mc_system_autotune(s)
+        mc.mc_mlem_init(s, y, x)
+        mc.mlem_iterate(s, y, x, n_iter)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mc.mc_mlem_init(s, y, x)
+        mc.mlem_iterate(s, y, x, n_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    sizes = sorted({int(ph.shape[0]) for ph, _, _, _ in mix})
+    out = {"phantoms": n_phantoms, "grids": sizes, "histories_per_phantom": histories, "mlem_iters": n_iter,
+           "build_s": build_s, "batch_ms": batch_ms, "images_per_s": n_phantoms / (batch_ms * 1e-3),
+           "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+           "sequential_images_per_s": n_phantoms / (sum(lat) * 1e-3),
+           "nnz_total": int(sum(s.info()["nnz"] for s in systems))}
+    batch.free()
+    for s in systems:
+        s.free()
+    return out
+
+
 def run_ours(args, w):
     import torch
 
@@ -376,6 +429,9 @@ def run_ours(args, w):
     roof = None
     if args.roof_histories and rank == 0:
         roof = roof_instance(mc, plan, int(args.roof_histories), seed, n_iter, flush, stream, hbm_gbs, peak_kind)
+    serving = None
+    if args.serving_phantoms and rank == 0:
+        serving = serving_benchmark(mc, int(args.serving_phantoms), int(args.serving_histories), 30, stream)
 
     # transport roofline (lane-op issue bound), work counted from an FP64
     # trace of a history sample of this workload
@@ -448,6 +504,7 @@ def run_ours(args, w):
                               "traffic": None, "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
                               "note": "benchmark matrix (largely L2-resident)"},
             "roofline_mlem_roof": roof,
+            "serving": serving,
             "mlem_value_types": value_types,
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -475,6 +532,8 @@ def main(argv=None):
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-phantoms", type=int, default=64, help="mixed serving batch size (0: skip)")
+    ap.add_argument("--serving-histories", type=float, default=2e7, help="histories per serving phantom")
     ap.add_argument("--roof-histories", type=float, default=1e11,
                     help="histories of the large-matrix SpMV roofline instance (0: skip)")
     args = ap.parse_args(argv)
