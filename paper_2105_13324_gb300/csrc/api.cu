@@ -73,6 +73,7 @@ int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, do
 int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const float *gp, float *x, cudaStream_t s);
 int batch_create(mc_system *const *sys, int n, const float *const *y, float *const *x, mc_batch **out);
 int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s);
+void batch_free(mc_batch *b);
 int autotune(mc_system *sys, cudaStream_t s, int *fwd_choice, int *bwd_choice);
 void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
                           std::vector<float> &sig_tab);
@@ -719,7 +720,7 @@ int mc_batch_mlem(mc_batch *batch, int32_t n_iter, void *stream) {
 
 int mc_batch_free(mc_batch *batch) {
   clear_error();
-  delete batch;
+  batch_free(batch);
   return MC_OK;
 }
 

@@ -360,17 +360,19 @@ __global__ void max_segment_kernel(const uint32_t *ptr, int64_t n, unsigned int 
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
-// tiles[b] = first segment whose start is >= b * step (tiles[n_tiles] = n).
-// With step = kStreamTile - longest segment, each tile holds fewer than
-// kStreamTile entries.
+// tiles[b] = first segment i with ptr[i] + i >= b * step (tiles[n_tiles] = n):
+// the measure counts entries and segments, so a tile holds at most step +
+// longest of the two together.  With step = kStreamTile - longest - 1 every
+// tile has fewer than kStreamTile entries and rows, however sparse the
+// matrix.
 __global__ void tile_bounds_kernel(const uint32_t *ptr, int64_t n, uint32_t step, int64_t n_tiles, uint32_t *tiles) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= n_tiles; b += (int64_t)gridDim.x * blockDim.x) {
     if (b == n_tiles) { tiles[b] = (uint32_t)n; continue; }
     const uint64_t target = (uint64_t)b * step;
-    int64_t lo = 0, hi = n;  // first i in [0, n] with ptr[i] >= target
+    int64_t lo = 0, hi = n;  // first i in [0, n] with ptr[i] + i >= target
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
-      if ((uint64_t)ptr[mid] >= target) hi = mid; else lo = mid + 1;
+      if ((uint64_t)ptr[mid] + (uint64_t)mid >= target) hi = mid; else lo = mid + 1;
     }
     tiles[b] = (uint32_t)lo;
   }
@@ -483,10 +485,11 @@ int forward_blocks(const mc_system *sys) {
   return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads);
 }
 
-// Tiles for one pointer array: none (row-group kernels) when a segment is
-// longer than half a tile.
+// Tiles for one pointer array.  Unless `force`, none (row-group kernels)
+// when a segment is longer than half a tile or the mean segment is long;
+// with `force` a segment longer than half a tile is an error.
 static int stream_tiles(const DevBuf &ptr, int64_t n, int64_t nnz, DevBuf &tiles, int64_t &n_tiles, bool &warp,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool force = false) {
   n_tiles = 0;
   if (n <= 0 || nnz <= 0) return MC_OK;
   DevBuf mx;
@@ -498,10 +501,15 @@ static int stream_tiles(const DevBuf &ptr, int64_t n, int64_t nnz, DevBuf &tiles
   unsigned int longest = 0;
   MCS_CUDA(cudaMemcpyAsync(&longest, mx.p, sizeof(longest), cudaMemcpyDeviceToHost, s));
   MCS_CUDA(cudaStreamSynchronize(s));
+  if ((int64_t)longest * 2 > kStreamTile) {
+    if (!force) return MC_OK;
+    set_error("segment of %u entries is too long for a streaming tile", longest);
+    return MC_EINVAL;
+  }
   // tiles pay off for short segments; long ones stream better per row group
-  if ((int64_t)longest * 2 > kStreamTile || (double)nnz / (double)n >= 32.0) return MC_OK;
-  const uint32_t step = (uint32_t)(kStreamTile - longest);
-  n_tiles = (nnz + step - 1) / step;
+  if (!force && (double)nnz / (double)n >= 32.0) return MC_OK;
+  const uint32_t step = (uint32_t)(kStreamTile - longest - 1);
+  n_tiles = (nnz + n + step - 1) / step;
   MCS_TRY(tiles.alloc((size_t)(n_tiles + 1) * sizeof(uint32_t), s));
   count_launch();
   tile_bounds_kernel<<<grid_stride_blocks(n_tiles + 1), 256, 0, s>>>(ptr.as<uint32_t>(), n, step, n_tiles,
@@ -868,17 +876,33 @@ int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const
 // Each iteration is one forward launch over the concatenated CSR tiles of
 // all systems and one back-projection launch over their CSC tiles; a block
 // finds its system by binary search in the prefix of tile counts.  The
-// whole reconstruction (start images + n_iter iterations) is captured once
-// in a CUDA graph and replayed.
+// whole reconstruction (start images, n_iter iterations, write-back of the
+// images) is captured once in a CUDA graph and replayed.
+//
+// Serving systems are built from few histories, so most of their rows and
+// columns are empty.  The batch renumbers each system onto its non-empty
+// rows and columns only: compacted pointers, row/column indices relabelled
+// to compacted positions, and per-system compacted vectors (y, ratio, image,
+// scaled image, 1/S, 1/n_v).  An empty row's ratio is never read (no column
+// refers to it), and an empty column has S_v = 0, so the start image sets it
+// to 0 and the update keeps it there: the iterates are those of the full
+// system.  An iteration then streams bytes in proportion to the non-zeros,
+// and the gathered vectors (4 bytes per non-empty column or row) stay in L2.
 namespace mcs {
 
 struct BatchSys {
-  const uint32_t *row_ptr, *csr_tiles, *col_idx, *col_ptr, *csc_tiles, *row_idx;
-  const float *csr_val, *csc_val, *inv_n, *inv_colsum, *y;
-  const double *colsum;
-  const uint32_t *n_v;
-  float *x, *xs, *r;
-  int64_t n_rows, n_cols;
+  // compacted CSR: segment j is row row_id[j], entries [row_ptr[j],
+  // row_ptr[j + 1]) with column indices in compacted column numbering
+  const uint32_t *row_ptr, *row_id, *csr_tiles, *col_idx;
+  // compacted CSC: segment j is column col_id[j]; row indices compacted
+  const uint32_t *col_ptr, *col_id, *csc_tiles, *row_idx;
+  const float *csr_val, *csc_val;
+  const float *y;            // measured data, all n_rows rows
+  float *x;                  // image, all n_cols voxels
+  float *y_c, *r_c;          // per non-empty row: data, ratio y / (A x)
+  float *x_c, *xs_c;         // per non-empty column: image, image / n_v
+  const float *ics_c, *invn_c;  // per non-empty column: 1 / S_v, 1 / n_v
+  int64_t n_rows, n_cols, m_c, n_c;
   int warp_fwd, warp_bwd;
 };
 
@@ -891,26 +915,40 @@ __device__ __forceinline__ int batch_find(const uint64_t *off, int n, uint64_t i
   return lo;
 }
 
+// The block's system descriptor is copied to shared memory once, so that
+// stores through its output pointers cannot force reloads of the others.
+__device__ __forceinline__ const BatchSys &batch_desc(const BatchSys *systems, const uint64_t *off, int n_sys,
+                                                      BatchSys *s_desc, uint32_t &tile) {
+  const int k = batch_find(off, n_sys, blockIdx.x);
+  if (threadIdx.x == 0) *s_desc = systems[k];
+  tile = (uint32_t)(blockIdx.x - off[k]);
+  __syncthreads();
+  return *s_desc;
+}
+
 __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
                                                                     const uint64_t *__restrict__ tile_off,
                                                                     int n_sys) {
   __shared__ float s_prod[kStreamTile];
-  const int k = batch_find(tile_off, n_sys, blockIdx.x);
-  const BatchSys &S = systems[k];
-  const uint32_t tile = (uint32_t)(blockIdx.x - tile_off[k]);
-  const uint32_t r0 = S.csr_tiles[tile], r1 = S.csr_tiles[tile + 1];
-  const uint32_t p0 = S.row_ptr[r0];
-  stream_products<float>(p0, S.row_ptr[r1] - p0, S.col_idx, S.csr_val, S.xs, s_prod);
+  __shared__ BatchSys s_desc;
+  uint32_t tile;
+  const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
+  const uint32_t *__restrict__ ptr = S.row_ptr;
+  const float *__restrict__ y = S.y_c;
+  float *__restrict__ rout = S.r_c;
+  const uint32_t j0 = S.csr_tiles[tile], j1 = S.csr_tiles[tile + 1];
+  const uint32_t p0 = ptr[j0];
+  stream_products<float>(p0, ptr[j1] - p0, S.col_idx, S.csr_val, S.xs_c, s_prod);
   __syncthreads();
   if (S.warp_fwd) {
-    for (uint32_t r = r0 + (threadIdx.x >> 5); r < r1; r += kStreamThreads / 32) {
-      const float acc = stream_segment<true>(s_prod, S.row_ptr[r] - p0, S.row_ptr[r + 1] - p0);
-      if ((threadIdx.x & 31) == 0) S.r[r] = acc > 0.0f ? S.y[r] / acc : 0.0f;
+    for (uint32_t j = j0 + (threadIdx.x >> 5); j < j1; j += kStreamThreads / 32) {
+      const float acc = stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
+      if ((threadIdx.x & 31) == 0) rout[j] = acc > 0.0f ? y[j] / acc : 0.0f;
     }
   } else {
-    for (uint32_t r = r0 + threadIdx.x; r < r1; r += kStreamThreads) {
-      const float acc = stream_segment<false>(s_prod, S.row_ptr[r] - p0, S.row_ptr[r + 1] - p0);
-      S.r[r] = acc > 0.0f ? S.y[r] / acc : 0.0f;
+    for (uint32_t j = j0 + threadIdx.x; j < j1; j += kStreamThreads) {
+      const float acc = stream_segment<false>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
+      rout[j] = acc > 0.0f ? y[j] / acc : 0.0f;
     }
   }
 }
@@ -918,59 +956,149 @@ __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const Bat
 __global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchSys *__restrict__ systems,
                                                                  const uint64_t *__restrict__ tile_off, int n_sys) {
   __shared__ float s_prod[kStreamTile];
-  const int k = batch_find(tile_off, n_sys, blockIdx.x);
-  const BatchSys &S = systems[k];
-  const uint32_t tile = (uint32_t)(blockIdx.x - tile_off[k]);
-  const uint32_t c0 = S.csc_tiles[tile], c1 = S.csc_tiles[tile + 1];
-  const uint32_t p0 = S.col_ptr[c0];
-  stream_products<float>(p0, S.col_ptr[c1] - p0, S.row_idx, S.csc_val, S.r, s_prod);
+  __shared__ BatchSys s_desc;
+  uint32_t tile;
+  const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
+  const uint32_t *__restrict__ ptr = S.col_ptr;
+  const float *__restrict__ ics = S.ics_c;
+  const float *__restrict__ inv_n = S.invn_c;
+  float *__restrict__ x = S.x_c;
+  float *__restrict__ xs = S.xs_c;
+  const uint32_t j0 = S.csc_tiles[tile], j1 = S.csc_tiles[tile + 1];
+  const uint32_t p0 = ptr[j0];
+  stream_products<float>(p0, ptr[j1] - p0, S.row_idx, S.csc_val, S.r_c, s_prod);
   __syncthreads();
   const bool warp = S.warp_bwd != 0;
   const uint32_t first = warp ? (threadIdx.x >> 5) : threadIdx.x;
   const uint32_t step = warp ? kStreamThreads / 32 : kStreamThreads;
-  for (uint32_t v = c0 + first; v < c1; v += step) {
-    const float acc = warp ? stream_segment<true>(s_prod, S.col_ptr[v] - p0, S.col_ptr[v + 1] - p0)
-                           : stream_segment<false>(s_prod, S.col_ptr[v] - p0, S.col_ptr[v + 1] - p0);
+  for (uint32_t j = j0 + first; j < j1; j += step) {
+    const float acc = warp ? stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0)
+                           : stream_segment<false>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
     if (!warp || (threadIdx.x & 31) == 0) {
-      const float is = S.inv_colsum[v];
-      const float xn = is > 0.0f ? S.x[v] * acc * is : 0.0f;
-      S.x[v] = xn;
-      S.xs[v] = xn * S.inv_n[v];
+      const float is = ics[j];
+      const float xn = is > 0.0f ? x[j] * acc * is : 0.0f;
+      x[j] = xn;
+      xs[j] = xn * inv_n[j];
     }
   }
 }
 
-// start images: block k computes x0_k = sum(y_k) / sum(s_k)
-__global__ void batch_init_sums_kernel(const BatchSys *systems, double *x0) {
-  __shared__ double s_tmp[32];
-  const BatchSys &S = systems[blockIdx.x];
-  double ay = 0.0, as = 0.0;
-  for (int64_t i = threadIdx.x; i < S.n_rows; i += blockDim.x) ay += (double)S.y[i];
-  for (int64_t v = threadIdx.x; v < S.n_cols; v += blockDim.x)
-    if (S.n_v[v]) as += S.colsum[v] / (double)S.n_v[v];
-  const double ty = block_sum_double(ay, s_tmp);
-  const double ts = block_sum_double(as, s_tmp);
-  if (threadIdx.x == 0) x0[blockIdx.x] = ts > 0.0 ? ty / ts : 0.0;
+// Non-empty segments of a pointer array: flags (1 per non-empty segment,
+// 0 at index n), then after an exclusive scan of the flags each non-empty
+// segment i lands at pos[i] with its id and start; cptr[count] = ptr[n].
+__global__ void segment_flags_kernel(const uint32_t *ptr, int64_t n, uint32_t *flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = i < n && ptr[i + 1] > ptr[i] ? 1u : 0u;
 }
 
-__global__ void batch_init_fill_kernel(const BatchSys *systems, const uint64_t *vox_off, int n_sys, uint64_t total,
-                                       const double *x0) {
-  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
-    const int k = batch_find(vox_off, n_sys, g);
-    const BatchSys &S = systems[k];
-    const uint64_t v = g - vox_off[k];
-    const float xv = S.colsum[v] > 0.0 ? (float)x0[k] : 0.0f;
-    S.x[v] = xv;
-    S.xs[v] = xv * S.inv_n[v];
+__global__ void segment_compact_kernel(const uint32_t *ptr, int64_t n, const uint32_t *flags, const uint32_t *pos,
+                                       uint32_t *id, uint32_t *cptr) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == n) cptr[pos[n]] = ptr[n];
+    else if (flags[i]) { id[pos[i]] = (uint32_t)i; cptr[pos[i]] = ptr[i]; }
   }
+}
+
+// out[e] = pos[idx[e]]: entry indices in compacted numbering
+__global__ void relabel_kernel(const uint32_t *idx, int64_t nnz, const uint32_t *pos, uint32_t *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = pos[idx[e]];
+}
+
+__global__ void gather_f32_kernel(const float *src, const uint32_t *id, int64_t n, float *dst) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = src[id[j]];
+}
+
+// Start images: x0_k = sum(y_k) / sum(s_k).  The sensitivity totals are a
+// property of the systems and are summed once when the batch is made; sum(y)
+// runs over kInitChunks slices per system, then in a fixed order.  Every
+// per-system kernel below is a row of kInitChunks blocks per system.
+constexpr int kInitChunks = 64;
+__global__ void batch_sens_sums_kernel(const double *const *colsum, const uint32_t *const *n_v, const int64_t *n_cols,
+                                       double *part) {
+  __shared__ double s_tmp[32];
+  const int k = blockIdx.x / kInitChunks, c = blockIdx.x % kInitChunks;
+  const double *cs = colsum[k];
+  const uint32_t *nv = n_v[k];
+  double as = 0.0;
+  for (int64_t v = (int64_t)c * blockDim.x + threadIdx.x; v < n_cols[k]; v += (int64_t)kInitChunks * blockDim.x)
+    if (nv[v]) as += cs[v] / (double)nv[v];
+  const double ts = block_sum_double(as, s_tmp);
+  if (threadIdx.x == 0) part[blockIdx.x] = ts;
+}
+
+__device__ __forceinline__ const BatchSys &batch_row_desc(const BatchSys *systems, BatchSys *s_desc, int &k, int &c) {
+  k = blockIdx.x / kInitChunks;
+  c = blockIdx.x % kInitChunks;
+  if (threadIdx.x == 0) *s_desc = systems[k];
+  __syncthreads();
+  return *s_desc;
+}
+
+// partial sums of y, and x = 0 over the whole image (the non-empty columns
+// are written back at the end)
+__global__ void batch_init_sums_kernel(const BatchSys *systems, double *part) {
+  __shared__ double s_tmp[32];
+  __shared__ BatchSys s_desc;
+  int k, c;
+  const BatchSys &S = batch_row_desc(systems, &s_desc, k, c);
+  const float *__restrict__ y = S.y;
+  float *__restrict__ x = S.x;
+  const int64_t stride = (int64_t)kInitChunks * blockDim.x, first = (int64_t)c * blockDim.x + threadIdx.x;
+  double ay = 0.0;
+  for (int64_t i = first; i < S.n_rows; i += stride) ay += (double)y[i];
+  for (int64_t v = first; v < S.n_cols; v += stride) x[v] = 0.0f;
+  const double ty = block_sum_double(ay, s_tmp);
+  if (threadIdx.x == 0) part[blockIdx.x] = ty;
+}
+
+// x0[k] = (sum of part_y over k's chunks) / (sum of part_s over k's chunks)
+__global__ void batch_init_total_kernel(const double *part_y, const double *part_s, int n_sys, double *x0) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_sys; k += gridDim.x * blockDim.x) {
+    double sy = 0.0, ss = 0.0;
+    for (int c = 0; c < kInitChunks; ++c) {
+      sy += part_y[k * kInitChunks + c];
+      ss += part_s[k * kInitChunks + c];
+    }
+    x0[k] = ss > 0.0 ? sy / ss : 0.0;
+  }
+}
+
+// compacted data y_c, start image x_c = x0 (every compacted column has
+// S > 0), xs_c = x_c / n_v
+__global__ void batch_init_fill_kernel(const BatchSys *systems, const double *x0) {
+  __shared__ BatchSys s_desc;
+  int k, c;
+  const BatchSys &S = batch_row_desc(systems, &s_desc, k, c);
+  const int64_t stride = (int64_t)kInitChunks * blockDim.x, first = (int64_t)c * blockDim.x + threadIdx.x;
+  const float x0k = (float)x0[k];
+  for (int64_t j = first; j < S.m_c; j += stride) S.y_c[j] = S.y[S.row_id[j]];
+  for (int64_t j = first; j < S.n_c; j += stride) {
+    S.x_c[j] = x0k;
+    S.xs_c[j] = x0k * S.invn_c[j];
+  }
+}
+
+// image write-back: x[col_id[j]] = x_c[j]
+__global__ void batch_scatter_kernel(const BatchSys *systems) {
+  __shared__ BatchSys s_desc;
+  int k, c;
+  const BatchSys &S = batch_row_desc(systems, &s_desc, k, c);
+  const int64_t stride = (int64_t)kInitChunks * blockDim.x, first = (int64_t)c * blockDim.x + threadIdx.x;
+  for (int64_t j = first; j < S.n_c; j += stride) S.x[S.col_id[j]] = S.x_c[j];
 }
 
 }  // namespace mcs
 
+// Per system the batch owns kBatchBufs device buffers (see batch_create).
+constexpr int kBatchBufs = 14;
+
 struct mc_batch {
   int n = 0;
-  mcs::DevBuf systems, tile_fwd, tile_bwd, vox_off, x0;
-  uint64_t n_tiles_fwd = 0, n_tiles_bwd = 0, n_vox = 0;
+  mcs::DevBuf systems, tile_fwd, tile_bwd, x0, part_y, part_s;
+  std::vector<mcs::DevBuf> owned;  // kBatchBufs per system
+  uint64_t n_tiles_fwd = 0, n_tiles_bwd = 0;
   cudaGraphExec_t exec = nullptr;
   int exec_iters = -1;
   ~mc_batch() {
@@ -980,9 +1108,54 @@ struct mc_batch {
 
 namespace mcs {
 
+// The non-empty segments of (ptr, n): their ids, compacted pointers and
+// stream tiles, and `relabel_out` = `relabel_in` (nnz indices into this
+// numbering, from the other orientation) in compacted numbering.
+// `scratch` holds 2 (n + 1) words.
+static int batch_segments(const uint32_t *ptr, int64_t n, int64_t nnz, const uint32_t *relabel_in, uint32_t *scratch,
+                          DevBuf &id, DevBuf &cptr, DevBuf &tiles, DevBuf &relabel_out, int64_t &count, int64_t &n_tiles,
+                          int &warp, cudaStream_t s) {
+  uint32_t *flags = scratch, *pos = scratch + (n + 1);
+  count_launch();
+  segment_flags_kernel<<<grid_stride_blocks(n + 1), 256, 0, s>>>(ptr, n, flags);
+  MCS_LAUNCHED();
+  MCS_TRY(exclusive_scan_u32(flags, pos, n + 1, s));
+  uint32_t cnt = 0;
+  MCS_CUDA(cudaMemcpyAsync(&cnt, pos + n, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  count = cnt;
+  MCS_TRY(id.alloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(uint32_t), s));
+  MCS_TRY(cptr.alloc((size_t)(cnt + 1) * sizeof(uint32_t), s));
+  MCS_TRY(relabel_out.alloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(uint32_t), s));
+  count_launch();
+  segment_compact_kernel<<<grid_stride_blocks(n + 1), 256, 0, s>>>(ptr, n, flags, pos, id.as<uint32_t>(),
+                                                                    cptr.as<uint32_t>());
+  MCS_LAUNCHED();
+  if (nnz > 0) {
+    count_launch();
+    relabel_kernel<<<grid_stride_blocks(nnz), 256, 0, s>>>(relabel_in, nnz, pos, relabel_out.as<uint32_t>());
+    MCS_LAUNCHED();
+  }
+  n_tiles = 0;
+  warp = 0;
+  if (cnt == 0) return MC_OK;
+  bool w = false;
+  MCS_TRY(stream_tiles(cptr, cnt, nnz, tiles, n_tiles, w, s, true));
+  warp = w ? 1 : 0;
+  return MC_OK;
+}
+
+// Per system k the batch owns, in owned[k * kBatchBufs + i]:
+//   0 row ids  1 row pointers  2 CSR tiles  3 column indices (compacted)
+//   4 col ids  5 col pointers  6 CSC tiles  7 row indices (compacted)
+//   8 y_c  9 r_c  10 x_c  11 xs_c  12 1/S (compacted)  13 1/n_v (compacted)
 int batch_create(mc_system *const *sys, int n, const float *const *y, float *const *x, mc_batch **out) {
   std::vector<BatchSys> hs(n);
-  std::vector<uint64_t> tf(n + 1, 0), tb(n + 1, 0), vo(n + 1, 0);
+  std::vector<uint64_t> tf(n + 1, 0), tb(n + 1, 0);
+  std::vector<const double *> h_colsum(n);
+  std::vector<const uint32_t *> h_nv(n);
+  std::vector<int64_t> h_ncols(n);
+  int64_t longest_vec = 1;
   for (int k = 0; k < n; ++k) {
     const mc_system *s = sys[k];
     if (!s || !y[k] || !x[k]) { set_error("batch entry %d: NULL system or vector", k); return MC_EINVAL; }
@@ -990,41 +1163,84 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
       set_error("batch entry %d: needs a full FP32 system with streaming tiles (short rows)", k);
       return MC_EINVAL;
     }
-    BatchSys &b = hs[k];
-    b.row_ptr = s->row_ptr.as<uint32_t>(); b.csr_tiles = s->csr_blocks.as<uint32_t>(); b.col_idx = s->col_idx.as<uint32_t>();
-    b.col_ptr = s->col_ptr.as<uint32_t>(); b.csc_tiles = s->csc_blocks.as<uint32_t>(); b.row_idx = s->row_idx.as<uint32_t>();
-    b.csr_val = s->csr_val.as<float>(); b.csc_val = s->csc_val.as<float>();
-    b.inv_n = s->inv_n.as<float>(); b.inv_colsum = s->inv_colsum.as<float>(); b.y = y[k];
-    b.colsum = s->colsum.as<double>(); b.n_v = s->n_v.as<uint32_t>();
-    b.x = x[k]; b.xs = s->xs.as<float>(); b.r = s->r.as<float>();
-    b.n_rows = s->n_rows; b.n_cols = s->n_cols;
-    b.warp_fwd = s->warp_rows_fwd; b.warp_bwd = s->warp_rows_bwd;
-    tf[k + 1] = tf[k] + (uint64_t)s->n_csr_blocks;
-    tb[k + 1] = tb[k] + (uint64_t)s->n_csc_blocks;
-    vo[k + 1] = vo[k] + (uint64_t)s->n_cols;
+    longest_vec = std::max<int64_t>(longest_vec, std::max(s->n_rows, s->n_cols) + 1);
   }
-  if (tf[n] >= (1ull << 31) || tb[n] >= (1ull << 31)) { set_error("too many tiles for one launch"); return MC_EINVAL; }
   mc_batch *b = new (std::nothrow) mc_batch();
   if (!b) { set_error("out of host memory"); return MC_ENOMEM; }
   auto fail = [&](int rc) { delete b; return rc; };
   cudaStream_t s = nullptr;
   int rc;
+  b->owned.resize((size_t)n * kBatchBufs);
+  {
+    DevBuf scratch;
+    if ((rc = scratch.alloc((size_t)2 * longest_vec * sizeof(uint32_t), s))) return fail(rc);
+    for (int k = 0; k < n; ++k) {
+      const mc_system *m = sys[k];
+      DevBuf *o = &b->owned[(size_t)k * kBatchBufs];
+      int64_t nt_f = 0, nt_b = 0, m_c = 0, n_c = 0;
+      BatchSys &d = hs[k];
+      // rows: compacted CSR segments, and the CSC's row indices relabelled
+      if ((rc = batch_segments(m->row_ptr.as<uint32_t>(), m->n_rows, m->nnz, m->row_idx.as<uint32_t>(),
+                               scratch.as<uint32_t>(), o[0], o[1], o[2], o[7], m_c, nt_f, d.warp_fwd, s)) ||
+          (rc = batch_segments(m->col_ptr.as<uint32_t>(), m->n_cols, m->nnz, m->col_idx.as<uint32_t>(),
+                               scratch.as<uint32_t>(), o[4], o[5], o[6], o[3], n_c, nt_b, d.warp_bwd, s)))
+        return fail(rc);
+      for (int i = 8; i < 10; ++i)
+        if ((rc = o[i].alloc((size_t)std::max<int64_t>(m_c, 1) * sizeof(float), s))) return fail(rc);
+      for (int i = 10; i < 14; ++i)
+        if ((rc = o[i].alloc((size_t)std::max<int64_t>(n_c, 1) * sizeof(float), s))) return fail(rc);
+      if (n_c > 0) {
+        count_launch();
+        gather_f32_kernel<<<grid_stride_blocks(n_c), 256, 0, s>>>(m->inv_colsum.as<float>(), o[4].as<uint32_t>(), n_c,
+                                                                  o[12].as<float>());
+        count_launch();
+        gather_f32_kernel<<<grid_stride_blocks(n_c), 256, 0, s>>>(m->inv_n.as<float>(), o[4].as<uint32_t>(), n_c,
+                                                                  o[13].as<float>());
+        if (cudaGetLastError() != cudaSuccess) { set_error("batch gather failed"); return fail(MC_ECUDA); }
+      }
+      d.row_id = o[0].as<uint32_t>(); d.row_ptr = o[1].as<uint32_t>(); d.csr_tiles = o[2].as<uint32_t>();
+      d.col_idx = o[3].as<uint32_t>();
+      d.col_id = o[4].as<uint32_t>(); d.col_ptr = o[5].as<uint32_t>(); d.csc_tiles = o[6].as<uint32_t>();
+      d.row_idx = o[7].as<uint32_t>();
+      d.csr_val = m->csr_val.as<float>(); d.csc_val = m->csc_val.as<float>();
+      d.y = y[k]; d.x = x[k];
+      d.y_c = o[8].as<float>(); d.r_c = o[9].as<float>(); d.x_c = o[10].as<float>(); d.xs_c = o[11].as<float>();
+      d.ics_c = o[12].as<float>(); d.invn_c = o[13].as<float>();
+      d.n_rows = m->n_rows; d.n_cols = m->n_cols; d.m_c = m_c; d.n_c = n_c;
+      tf[k + 1] = tf[k] + (uint64_t)nt_f;
+      tb[k + 1] = tb[k] + (uint64_t)nt_b;
+      h_colsum[k] = m->colsum.as<double>(); h_nv[k] = m->n_v.as<uint32_t>(); h_ncols[k] = m->n_cols;
+    }
+    MCS_CUDA(cudaStreamSynchronize(s));  // scratch is released on s after the last compaction
+  }
+  if (tf[n] >= (1ull << 31) || tb[n] >= (1ull << 31)) { set_error("too many tiles for one launch"); return fail(MC_EINVAL); }
+  DevBuf d_cs, d_nv, d_nc;
   if ((rc = b->systems.alloc(n * sizeof(BatchSys), s)) || (rc = b->tile_fwd.alloc((n + 1) * 8, s)) ||
-      (rc = b->tile_bwd.alloc((n + 1) * 8, s)) || (rc = b->vox_off.alloc((n + 1) * 8, s)) ||
-      (rc = b->x0.alloc(n * sizeof(double), s)))
+      (rc = b->tile_bwd.alloc((n + 1) * 8, s)) || (rc = b->x0.alloc(n * sizeof(double), s)) ||
+      (rc = b->part_y.alloc((size_t)n * kInitChunks * sizeof(double), s)) ||
+      (rc = b->part_s.alloc((size_t)n * kInitChunks * sizeof(double), s)) ||
+      (rc = d_cs.alloc(n * sizeof(double *), s)) || (rc = d_nv.alloc(n * sizeof(uint32_t *), s)) ||
+      (rc = d_nc.alloc(n * sizeof(int64_t), s)))
     return fail(rc);
   if (cudaMemcpyAsync(b->systems.p, hs.data(), n * sizeof(BatchSys), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->tile_fwd.p, tf.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b->tile_bwd.p, tb.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b->vox_off.p, vo.data(), (n + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaMemcpyAsync(d_cs.p, h_colsum.data(), n * sizeof(double *), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_nv.p, h_nv.data(), n * sizeof(uint32_t *), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_nc.p, h_ncols.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
     set_error("batch upload failed");
+    return fail(MC_ECUDA);
+  }
+  count_launch();
+  batch_sens_sums_kernel<<<n * kInitChunks, 256, 0, s>>>(d_cs.as<const double *>(), d_nv.as<const uint32_t *>(),
+                                                         d_nc.as<int64_t>(), b->part_s.as<double>());
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("batch sensitivity sums failed");
     return fail(MC_ECUDA);
   }
   b->n = n;
   b->n_tiles_fwd = tf[n];
   b->n_tiles_bwd = tb[n];
-  b->n_vox = vo[n];
   *out = b;
   return MC_OK;
 }
@@ -1032,11 +1248,14 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
 // Enqueue the whole batched reconstruction on s (used once for capture).
 static int batch_enqueue(mc_batch *b, int n_iter, cudaStream_t s) {
   const BatchSys *sys = b->systems.as<BatchSys>();
+  const unsigned rows = (unsigned)(b->n * kInitChunks);
   count_launch();
-  batch_init_sums_kernel<<<b->n, 1024, 0, s>>>(sys, b->x0.as<double>());
+  batch_init_sums_kernel<<<rows, 256, 0, s>>>(sys, b->part_y.as<double>());
   count_launch();
-  batch_init_fill_kernel<<<grid_stride_blocks((int64_t)b->n_vox), 256, 0, s>>>(sys, b->vox_off.as<uint64_t>(), b->n,
-                                                                               b->n_vox, b->x0.as<double>());
+  batch_init_total_kernel<<<div_up(b->n, 256), 256, 0, s>>>(b->part_y.as<double>(), b->part_s.as<double>(), b->n,
+                                                            b->x0.as<double>());
+  count_launch();
+  batch_init_fill_kernel<<<rows, 256, 0, s>>>(sys, b->x0.as<double>());
   for (int it = 0; it < n_iter; ++it) {
     if (b->n_tiles_fwd) {
       count_launch();
@@ -1047,6 +1266,8 @@ static int batch_enqueue(mc_batch *b, int n_iter, cudaStream_t s) {
       batch_back_kernel<<<(unsigned)b->n_tiles_bwd, kStreamThreads, 0, s>>>(sys, b->tile_bwd.as<uint64_t>(), b->n);
     }
   }
+  count_launch();
+  batch_scatter_kernel<<<rows, 256, 0, s>>>(sys);
   MCS_LAUNCHED();
   return MC_OK;
 }
@@ -1073,6 +1294,8 @@ int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s) {
   MCS_CUDA(cudaGraphLaunch(b->exec, s));
   return MC_OK;
 }
+
+void batch_free(mc_batch *b) { delete b; }
 
 // ---------------------------------------------------------------------------
 // SpMV autotuner: per system, the fastest of the streaming tiles and the row
