@@ -249,14 +249,35 @@ __global__ void sensitivity_kernel(const double *colsum, const uint32_t *n_v, in
 constexpr int kStreamTile = 4096;
 constexpr int kStreamThreads = 256;
 
+// Products of the tile's entries [p0, p0 + cnt) into s_prod.  The index
+// and value streams are read as aligned quads (16-byte index loads, two
+// quads per thread in flight); the partial quads at the two ends of the
+// tile take scalar loads.
 template <typename V>
 __device__ __forceinline__ void stream_products(uint32_t p0, uint32_t cnt, const uint32_t *__restrict__ idx,
                                                 const V *__restrict__ val, const float *__restrict__ vec,
                                                 float *s_prod) {
-#pragma unroll 4
-  for (uint32_t i = threadIdx.x; i < cnt; i += kStreamThreads) {
-    const uint32_t k = p0 + i;
-    s_prod[i] = to_f(__ldcs(val + k)) * __ldg(vec + __ldcs(idx + k));
+  const uint32_t h = p0 & 3u;                  // entries of the first quad before p0
+  const uint32_t nq = (h + cnt + 3u) >> 2;      // quads covering [p0 - h, p0 + cnt)
+  const uint32_t base = p0 - h;
+#pragma unroll 2
+  for (uint32_t q = threadIdx.x; q < nq; q += kStreamThreads) {
+    const int32_t i0 = (int32_t)(4u * q) - (int32_t)h;  // tile offset of the quad's first entry
+    if (i0 >= 0 && i0 + 4 <= (int32_t)cnt) {
+      const uint4 c = __ldcs(reinterpret_cast<const uint4 *>(idx + base) + q);
+      float v[4];
+      load4(val + base + 4u * q, v);
+      s_prod[i0] = v[0] * __ldg(vec + c.x);
+      s_prod[i0 + 1] = v[1] * __ldg(vec + c.y);
+      s_prod[i0 + 2] = v[2] * __ldg(vec + c.z);
+      s_prod[i0 + 3] = v[3] * __ldg(vec + c.w);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t i = i0 + u;
+        if (i >= 0 && i < (int32_t)cnt) s_prod[i] = to_f(__ldcs(val + p0 + i)) * __ldg(vec + __ldcs(idx + p0 + i));
+      }
+    }
   }
 }
 
@@ -275,6 +296,100 @@ __device__ __forceinline__ float stream_segment(const float *s_prod, uint32_t b,
   return acc;
 }
 
+// Reduces every segment j in [j0, j1) of the tile from shared memory and
+// hands its sum to out.store(j, acc, out.load(j)).  Warp mode: one warp per
+// segment.  Thread mode: each thread takes kSegBatch segments kStreamThreads
+// apart and issues their pointer loads and out.load() before any reduction,
+// so that short segments do not leave one load in flight per thread.
+constexpr int kSegBatch = 4;
+template <typename Out>
+__device__ __forceinline__ void stream_segments_thread(const uint32_t *__restrict__ ptr, uint32_t j0, uint32_t j1,
+                                                       uint32_t p0, const float *s_prod, Out &out) {
+  for (uint32_t base = j0 + threadIdx.x; base < j1; base += kSegBatch * kStreamThreads) {
+    uint32_t b[kSegBatch], e[kSegBatch];
+    typename Out::Pre pre[kSegBatch] = {};
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const uint32_t j = base + u * kStreamThreads;
+      b[u] = e[u] = p0;
+      if (j < j1) {
+        b[u] = ptr[j];
+        e[u] = ptr[j + 1];
+        pre[u] = out.load(j);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const uint32_t j = base + u * kStreamThreads;
+      if (j < j1) out.store(j, stream_segment<false>(s_prod, b[u] - p0, e[u] - p0), pre[u]);
+    }
+  }
+}
+
+template <bool WARP, typename Out>
+__device__ __forceinline__ void stream_segments(const uint32_t *__restrict__ ptr, uint32_t j0, uint32_t j1,
+                                                uint32_t p0, const float *s_prod, Out &out) {
+  if (WARP) {
+    for (uint32_t j = j0 + (threadIdx.x >> 5); j < j1; j += kStreamThreads / 32) {
+      const float acc = stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
+      if ((threadIdx.x & 31) == 0) out.store(j, acc, out.load(j));
+    }
+  } else {
+    stream_segments_thread(ptr, j0, j1, p0, s_prod, out);
+  }
+}
+
+// Forward epilogue: MODE 0 q, MODE 1 ratio (+ log-likelihood share),
+// MODE 2 ratio with row map and additive term (see ratio_out).
+template <int MODE, bool LL>
+struct FwdOut {
+  using Pre = float;
+  const float *__restrict__ y;
+  float *__restrict__ out;
+  const uint32_t *__restrict__ rmap;
+  const float *__restrict__ add;
+  double ll;
+  __device__ __forceinline__ float load(uint32_t r) const { return (MODE == 1) ? y[r] : 0.0f; }
+  __device__ __forceinline__ void store(uint32_t r, float acc, float yv) {
+    if (MODE == 0) {
+      out[r] = acc;
+    } else if (MODE == 1) {
+      out[r] = acc > 0.0f ? yv / acc : 0.0f;
+      if (LL) ll += (yv > 0.0f ? (double)yv * log((double)acc) : 0.0) - (double)acc;
+    } else {
+      out[r] = ratio_out<MODE>(acc, r, y, rmap, add);
+    }
+  }
+};
+
+// Back-projection epilogue: MODE 0 A^T r, MODE 1 EM update (0 where S = 0),
+// MODE 3 EM update keeping x where S = 0.
+struct BackPre { float is, x, inv_n; };
+template <int MODE>
+struct BackOut {
+  using Pre = BackPre;
+  const float *__restrict__ inv_n;
+  const float *__restrict__ inv_colsum;
+  float *__restrict__ x;
+  float *__restrict__ xs;
+  __device__ __forceinline__ BackPre load(uint32_t v) const {
+    BackPre p;
+    p.inv_n = inv_n[v];
+    p.is = MODE == 0 ? 0.0f : inv_colsum[v];
+    p.x = MODE == 0 ? 0.0f : x[v];
+    return p;
+  }
+  __device__ __forceinline__ void store(uint32_t v, float acc, const BackPre &p) const {
+    if (MODE == 0) {
+      x[v] = acc * p.inv_n;
+    } else {
+      const float xn = p.is > 0.0f ? p.x * acc * p.is : (MODE == 3 ? p.x : 0.0f);
+      x[v] = xn;
+      xs[v] = xn * p.inv_n;
+    }
+  }
+};
+
 template <typename V, bool WARP, int MODE, bool LL>
 __global__ void __launch_bounds__(kStreamThreads) stream_forward_kernel(const uint32_t *__restrict__ row_ptr,
                                                                      const uint32_t *__restrict__ tiles,
@@ -291,25 +406,10 @@ __global__ void __launch_bounds__(kStreamThreads) stream_forward_kernel(const ui
   const uint32_t p0 = row_ptr[r0];
   stream_products<V>(p0, row_ptr[r1] - p0, col, val, xs, s_prod);
   __syncthreads();
-  double ll = 0.0;
-  const uint32_t first = WARP ? (threadIdx.x >> 5) : threadIdx.x;
-  const uint32_t step = WARP ? kStreamThreads / 32 : kStreamThreads;
-  for (uint32_t r = r0 + first; r < r1; r += step) {
-    const float acc = stream_segment<WARP>(s_prod, row_ptr[r] - p0, row_ptr[r + 1] - p0);
-    if (!WARP || (threadIdx.x & 31) == 0) {
-      if (MODE == 0) {
-        out[r] = acc;
-      } else {
-        out[r] = ratio_out<MODE>(acc, r, y, rmap, add);
-        if (LL) {
-          const float yj = y[r];
-          ll += (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
-        }
-      }
-    }
-  }
+  FwdOut<MODE, LL> o{y, out, rmap, add, 0.0};
+  stream_segments<WARP>(row_ptr, r0, r1, p0, s_prod, o);
   if (LL) {
-    const double t = block_sum_double(ll, s_tmp);
+    const double t = block_sum_double(o.ll, s_tmp);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
@@ -328,21 +428,8 @@ __global__ void __launch_bounds__(kStreamThreads) stream_back_kernel(const uint3
   const uint32_t p0 = col_ptr[c0];
   stream_products<V>(p0, col_ptr[c1] - p0, row, val, r, s_prod);
   __syncthreads();
-  const uint32_t first = WARP ? (threadIdx.x >> 5) : threadIdx.x;
-  const uint32_t step = WARP ? kStreamThreads / 32 : kStreamThreads;
-  for (uint32_t v = c0 + first; v < c1; v += step) {
-    const float acc = stream_segment<WARP>(s_prod, col_ptr[v] - p0, col_ptr[v + 1] - p0);
-    if (!WARP || (threadIdx.x & 31) == 0) {
-      if (MODE == 0) {
-        x[v] = acc * inv_n[v];
-      } else {
-        const float is = inv_colsum[v];
-        const float xn = is > 0.0f ? x[v] * acc * is : (MODE == 3 ? x[v] : 0.0f);
-        x[v] = xn;
-        xs[v] = xn * inv_n[v];
-      }
-    }
-  }
+  BackOut<MODE> o{inv_n, inv_colsum, x, xs};
+  stream_segments<WARP>(col_ptr, c0, c1, p0, s_prod, o);
 }
 
 // longest segment of a CSR/CSC pointer array
@@ -926,6 +1013,16 @@ __device__ __forceinline__ const BatchSys &batch_desc(const BatchSys *systems, c
   return *s_desc;
 }
 
+// batch epilogues on compacted vectors: r_c = y_c / q (0 where q = 0);
+// x_c <- x_c t / S, xs_c = x_c / n_v
+struct BatchFwdOut {
+  using Pre = float;
+  const float *__restrict__ y;
+  float *__restrict__ r;
+  __device__ __forceinline__ float load(uint32_t j) const { return y[j]; }
+  __device__ __forceinline__ void store(uint32_t j, float acc, float yv) const { r[j] = acc > 0.0f ? yv / acc : 0.0f; }
+};
+
 __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
                                                                     const uint64_t *__restrict__ tile_off,
                                                                     int n_sys) {
@@ -934,23 +1031,13 @@ __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const Bat
   uint32_t tile;
   const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
   const uint32_t *__restrict__ ptr = S.row_ptr;
-  const float *__restrict__ y = S.y_c;
-  float *__restrict__ rout = S.r_c;
   const uint32_t j0 = S.csr_tiles[tile], j1 = S.csr_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
   stream_products<float>(p0, ptr[j1] - p0, S.col_idx, S.csr_val, S.xs_c, s_prod);
   __syncthreads();
-  if (S.warp_fwd) {
-    for (uint32_t j = j0 + (threadIdx.x >> 5); j < j1; j += kStreamThreads / 32) {
-      const float acc = stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
-      if ((threadIdx.x & 31) == 0) rout[j] = acc > 0.0f ? y[j] / acc : 0.0f;
-    }
-  } else {
-    for (uint32_t j = j0 + threadIdx.x; j < j1; j += kStreamThreads) {
-      const float acc = stream_segment<false>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
-      rout[j] = acc > 0.0f ? y[j] / acc : 0.0f;
-    }
-  }
+  BatchFwdOut o{S.y_c, S.r_c};
+  if (S.warp_fwd) stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
+  else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
 }
 
 __global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchSys *__restrict__ systems,
@@ -960,27 +1047,13 @@ __global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchS
   uint32_t tile;
   const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
   const uint32_t *__restrict__ ptr = S.col_ptr;
-  const float *__restrict__ ics = S.ics_c;
-  const float *__restrict__ inv_n = S.invn_c;
-  float *__restrict__ x = S.x_c;
-  float *__restrict__ xs = S.xs_c;
   const uint32_t j0 = S.csc_tiles[tile], j1 = S.csc_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
   stream_products<float>(p0, ptr[j1] - p0, S.row_idx, S.csc_val, S.r_c, s_prod);
   __syncthreads();
-  const bool warp = S.warp_bwd != 0;
-  const uint32_t first = warp ? (threadIdx.x >> 5) : threadIdx.x;
-  const uint32_t step = warp ? kStreamThreads / 32 : kStreamThreads;
-  for (uint32_t j = j0 + first; j < j1; j += step) {
-    const float acc = warp ? stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0)
-                           : stream_segment<false>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
-    if (!warp || (threadIdx.x & 31) == 0) {
-      const float is = ics[j];
-      const float xn = is > 0.0f ? x[j] * acc * is : 0.0f;
-      x[j] = xn;
-      xs[j] = xn * inv_n[j];
-    }
-  }
+  BackOut<1> o{S.invn_c, S.ics_c, S.x_c, S.xs_c};
+  if (S.warp_bwd) stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
+  else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
 }
 
 // Non-empty segments of a pointer array: flags (1 per non-empty segment,
