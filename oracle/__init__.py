@@ -8,7 +8,8 @@ reconstruction below is plain NumPy/SciPy in float64).
 Transport (paper Sec. 2, Sec. 5.1): ``run`` follows photon histories and
 returns tally events; ``system_counts`` turns events into the count matrix C
 whose columns, divided by the histories started in each voxel, estimate
-T_ij of Eq. (IMC).
+T_ij of Eq. (IMC).  ``run_fd`` is the forced-detection variant (the paper's
+variance-reduction section): weighted events, summed by ``system_weights``.
 
 Reconstruction (paper Sec. 5.1, Eq. (MLEM)):
     S_i^{k+1} = S_i^k / (sum_j T_ij) * sum_m P_m T_im / (sum_l S_l^k T_lm)
@@ -76,6 +77,7 @@ class _Problem(ctypes.Structure):
         ("fwhm_mm", ctypes.c_double), ("e0_kev", ctypes.c_double),
         ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double),
         ("primary_only", ctypes.c_int32),
+        ("forced_detection", ctypes.c_int32),
     ]
 
 
@@ -99,6 +101,16 @@ def lib():
             L.orc_run.argtypes = [P, u64, u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                                   ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)), ctypes.POINTER(ctypes.c_int64), vp]
             L.orc_run.restype = ctypes.c_int
+            L.orc_run_w.argtypes = [P, u64, u64, u64, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
+                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)), ctypes.POINTER(ctypes.c_int64), vp]
+            L.orc_run_w.restype = ctypes.c_int
+            L.orc_kn_pdf_sr.argtypes = [dbl, dbl]
+            L.orc_kn_pdf_sr.restype = dbl
+            L.orc_transmission.argtypes = [P, vp, vp, dbl]
+            L.orc_transmission.restype = dbl
+            L.orc_fd_point.argtypes = [P, u64, u64, ctypes.c_uint32, vp, vp, dbl, dbl, ctypes.c_int, vp, vp, i32]
+            L.orc_fd_point.restype = ctypes.c_int
             L.orc_free.argtypes = [vp]
             L.orc_beam.argtypes = [P, u64, u64, vp, vp, dbl]
             L.orc_beam.restype = u64
@@ -115,7 +127,7 @@ class Problem:
     """A phantom + geometry pair marshalled for the C oracle.  Keeps the
     NumPy buffers alive for as long as the struct is in use."""
 
-    def __init__(self, phantom, geometry, primary_only: bool = False):
+    def __init__(self, phantom, geometry, primary_only: bool = False, forced_detection: bool = False):
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -129,7 +141,8 @@ class Problem:
                           g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
                           float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
                           float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
-                          int(bool(primary_only)))
+                          int(bool(primary_only)), int(bool(forced_detection)))
+        self.forced_detection = bool(forced_detection)
 
     @property
     def ref(self):
@@ -201,6 +214,60 @@ def run(prob: Problem, seed: int, first: int, count: int, threads: int | None = 
     return rows, cols, fates
 
 
+def run_fd(prob: Problem, seed: int, first: int, count: int, threads: int | None = None):
+    """Forced detection (Problem(..., forced_detection=True)): histories
+    [first, first+count).  Returns (rows int32, cols int64, q int64, fates[4]),
+    q the fixed-point weights w * 2^48 rounded to the nearest integer."""
+    if not prob.forced_detection:
+        raise ValueError("run_fd needs a Problem with forced_detection=True")
+    if threads is None:
+        threads = os.cpu_count() or 1
+    L = lib()
+    rp = ctypes.POINTER(ctypes.c_int32)()
+    cp = ctypes.POINTER(ctypes.c_int64)()
+    qp = ctypes.POINTER(ctypes.c_int64)()
+    n = ctypes.c_int64(0)
+    fates = np.zeros(4, np.uint64)
+    rc = L.orc_run_w(prob.ref, seed, first, count, int(threads), ctypes.byref(rp), ctypes.byref(cp),
+                     ctypes.byref(qp), ctypes.byref(n), fates.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle transport ran out of memory")
+    ne = n.value
+    rows = np.ctypeslib.as_array(rp, shape=(max(ne, 1),))[:ne].copy()
+    cols = np.ctypeslib.as_array(cp, shape=(max(ne, 1),))[:ne].copy()
+    q = np.ctypeslib.as_array(qp, shape=(max(ne, 1),))[:ne].copy()
+    for ptr in (rp, cp, qp):
+        L.orc_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return rows, cols, q, fates
+
+
+FD_SCALE = 2.0 ** 48
+
+
+def kn_pdf_sr(e_kev: float, mu: float) -> float:
+    """Klein-Nishina angular density of the scattered direction, per sr."""
+    return lib().orc_kn_pdf_sr(float(e_kev), float(mu))
+
+
+def transmission(prob: Problem, p, d, e_kev: float) -> float:
+    """exp(-line integral of mu(E)) from p along d to the grid boundary."""
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    return lib().orc_transmission(prob.ref, pp.ctypes.data, dd.ctypes.data, float(e_kev))
+
+
+def fd_point(prob: Problem, seed: int, history: int, n: int, p, d_in, e_kev: float, p_keep: float,
+             emission: bool, max_rows: int = 4096):
+    """Forced copies of one interaction: (rows, q) over the views."""
+    pp = np.ascontiguousarray(p, dtype=np.float64)
+    dd = np.ascontiguousarray(d_in, dtype=np.float64)
+    rows = np.zeros(max_rows, np.int32)
+    qs = np.zeros(max_rows, np.int64)
+    k = lib().orc_fd_point(prob.ref, seed, history, int(n), pp.ctypes.data, dd.ctypes.data, float(e_kev),
+                           float(p_keep), int(bool(emission)), rows.ctypes.data, qs.ctypes.data, max_rows)
+    return rows[:min(k, max_rows)], qs[:min(k, max_rows)]
+
+
 def beam(prob: Problem, seed: int, n: int, p0, d, e_kev: float) -> int:
     p = np.ascontiguousarray(p0, dtype=np.float64)
     dd = np.ascontiguousarray(d, dtype=np.float64)
@@ -245,6 +312,32 @@ def system_counts(rows, cols, n_rows: int, n_voxels: int) -> sp.csc_matrix:
     m = sp.csc_matrix((cnt.astype(np.int64), (r, c)), shape=(n_rows, n_voxels))
     m.sort_indices()
     return m
+
+
+def system_weights(rows, cols, q, n_rows: int, n_voxels: int) -> sp.csc_matrix:
+    """Weighted tally W[j, v] = sum of the fixed-point weights q of the events
+    (j, v), summed as exact integers, returned as float64 (q * 2^-48) CSC
+    with sorted row indices (every sum is below 2^53 units, so exact)."""
+    key = np.asarray(cols, np.int64) * n_rows + np.asarray(rows, np.int64)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    qs = np.asarray(q, np.int64)[order]
+    if len(ks) == 0:
+        return sp.csc_matrix((n_rows, n_voxels), dtype=np.float64)
+    heads = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    uk = ks[heads]
+    sums = np.add.reduceat(qs, heads)
+    m = sp.csc_matrix((sums.astype(np.float64) / FD_SCALE, (uk % n_rows, uk // n_rows)), shape=(n_rows, n_voxels))
+    m.sort_indices()
+    return m
+
+
+def build_system_fd(prob: Problem, seed: int, n_histories: int, first: int = 0, threads=None):
+    """Forced-detection transport + tally: (A float64 CSR, W float64 CSC, n_v, fates)."""
+    rows, cols, q, fates = run_fd(prob, seed, first, n_histories, threads)
+    w = system_weights(rows, cols, q, prob.n_rows, prob.n_voxels)
+    n_v = histories_per_voxel(prob.n_voxels, first, n_histories)
+    return system_matrix(w, n_v), w, n_v, fates
 
 
 def system_matrix(counts: sp.spmatrix, n_v: np.ndarray) -> sp.csr_matrix:

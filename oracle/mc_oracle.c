@@ -31,6 +31,27 @@
  *       view's axis passes with probability f(x) = (2/pi)(acos x - x sqrt(1-x^2)),
  *       x = (L/d) tan psi, the overlap fraction of the two ends of a hole.
  *   R6  Gaussian intrinsic blur (FWHM) by Box-Muller on two draws.
+ *   R7  forced detection (the variance-reduction technique of the paper's
+ *       Sec. 4 on VRT: a copy of the photon is forced to the detector at
+ *       each interaction location and weighted by the probability of not
+ *       being absorbed there, of leaving in a direction the collimator
+ *       passes, and of crossing the medium unabsorbed).  Interaction
+ *       locations are the emission point (n = 0) and every real collision
+ *       (n = 1, 2, ...).  For each view k the copy's direction is drawn
+ *       uniformly in the cone of directions the collimator can pass
+ *       (tan(psi) < d/L about the view's normal) from its own stream
+ *       block, counter (k, 1 + n, h_lo, h_hi), which the analog stream never
+ *       reaches (its block index stays below 2^32).  Weight:
+ *         emission:  Omega_c / (4 pi) * f(x) * T(p, d, E0)
+ *         collision: (1 - mu_pe/mu) * Omega_c * p_KN(cos theta_s | E)
+ *                    * f(x) * T(p, d, E')   (0 if E' = eps E < E_low)
+ *       with Omega_c the cone's solid angle, p_KN the Klein-Nishina
+ *       angular density per steradian, T the exact transmission along the
+ *       ray to the grid boundary.  The copy is binned like an analog
+ *       detection (crystal hit, Gaussian blur on the block's last two
+ *       words); the analog photon itself is no longer detected.  Weights
+ *       are tallied in fixed point, q = rint(w 2^48), so that sums are
+ *       exact integers whatever their order.
  *
  * Precision: every floating-point value is an IEEE double.  Build with
  * -ffp-contract=off so that no multiply-add is fused and the results are the
@@ -73,6 +94,7 @@ typedef struct {
   double fwhm_mm;
   double e0_kev, window_frac, photo_k;
   int32_t primary_only; /* 1: tally only photons that never scattered */
+  int32_t forced_detection; /* 1: R7 forced detection instead of analog detection */
 } orc_problem;
 
 typedef struct {
@@ -314,9 +336,128 @@ static void detect(const orc_problem *pb, orc_stream *s, const double p[3], cons
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* R7: forced detection                                                      */
+/* ------------------------------------------------------------------------ */
+#define ORC_FD_SCALE 281474976710656.0 /* 2^48 */
+
+/* Klein-Nishina angular density of the scattered direction, per steradian:
+ * (dsigma/dOmega) / sigma_KN with dsigma/dOmega = (r_e^2 / 2) eps^2
+ * (eps + 1/eps - sin^2 theta), eps = 1 / (1 + alpha (1 - cos theta)). */
+double orc_kn_pdf_sr(double e_kev, double mu) {
+  double alpha = e_kev / ORC_MEC2_KEV;
+  double eps = 1.0 / (1.0 + alpha * (1.0 - mu));
+  double dsig = 0.5 * ORC_RE_CM * ORC_RE_CM * (eps * eps) * (eps + 1.0 / eps - (1.0 - mu * mu));
+  return dsig / orc_sigma_kn_cm2(e_kev);
+}
+
+/* exp(-integral of mu(E) along the ray p + t d, t >= 0, up to the grid
+ * boundary), by visiting the voxels the ray crosses in order (a 3-D DDA:
+ * the next voxel is across the nearest of the three next faces, ties to
+ * the lowest axis).  p must be inside the box; d a unit vector. */
+double orc_transmission(const orc_problem *pb, const double p[3], const double d[3], double e_kev) {
+  int n[3] = {pb->nx, pb->ny, pb->nz};
+  double h = pb->voxel_mm;
+  double mu_m[256];
+  for (int m = 0; m < pb->n_materials; ++m) mu_m[m] = orc_mu_total(pb, m, e_kev);
+  int idx[3], step[3];
+  double tn[3];
+  for (int a = 0; a < 3; ++a) {
+    double half = 0.5 * n[a] * h;
+    idx[a] = axis_index(p[a], n[a], h);
+    if (d[a] > 0.0) {
+      step[a] = 1;
+      tn[a] = ((-half + (idx[a] + 1) * h) - p[a]) / d[a];
+    } else if (d[a] < 0.0) {
+      step[a] = -1;
+      tn[a] = ((-half + idx[a] * h) - p[a]) / d[a];
+    } else {
+      step[a] = 0;
+      tn[a] = INFINITY;
+    }
+  }
+  double t = 0.0, sum = 0.0;
+  for (;;) {
+    int m = pb->material[((int64_t)idx[2] * pb->ny + idx[1]) * pb->nx + idx[0]];
+    int a = 0;
+    if (tn[1] < tn[a]) a = 1;
+    if (tn[2] < tn[a]) a = 2;
+    double t1 = tn[a];
+    if (t1 > t) {
+      sum += mu_m[m] * (t1 - t);
+      t = t1;
+    }
+    idx[a] += step[a];
+    if (idx[a] < 0 || idx[a] >= n[a]) break;
+    double half = 0.5 * n[a] * h;
+    tn[a] = ((-half + (idx[a] + (step[a] > 0 ? 1 : 0)) * h) - p[a]) / d[a];
+  }
+  return exp(-sum);
+}
+
+typedef void (*orc_emit_w_fn)(void *ctx, int32_t row, int64_t q);
+
+/* The forced copies of interaction n of history h (at p, energy e, incoming
+ * direction d_in; p_keep = 1 - mu_pe/mu at a collision, 1 at emission). */
+static void fd_point(const orc_problem *pb, uint64_t seed, uint64_t h, uint32_t n, const double p[3],
+                     const double d_in[3], double e, double p_keep, int emission, orc_emit_w_fn emit, void *ctx) {
+  double ratio = pb->hole_len_mm / pb->hole_diam_mm;
+  double sigma = pb->fwhm_mm / (2.0 * sqrt(2.0 * log(2.0)));
+  double plane = pb->radius_mm + pb->hole_len_mm;
+  double tan_max = pb->hole_diam_mm / pb->hole_len_mm;
+  double cos_max = 1.0 / sqrt(1.0 + tan_max * tan_max);
+  double omega = 2.0 * ORC_PI * (1.0 - cos_max);
+  double elow = e_low(pb);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int k = 0; k < pb->n_views; ++k) {
+    uint32_t ctr[4] = {(uint32_t)k, 1u + n, (uint32_t)h, (uint32_t)(h >> 32)}, w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double u0 = ((double)w[0] + 0.5) * (1.0 / 4294967296.0);
+    double u1 = ((double)w[1] + 0.5) * (1.0 / 4294967296.0);
+    double u2 = ((double)w[2] + 0.5) * (1.0 / 4294967296.0);
+    double u3 = ((double)w[3] + 0.5) * (1.0 / 4294967296.0);
+    double th = (pb->start_deg + k * (pb->arc_deg / pb->n_views)) * (ORC_PI / 180.0);
+    double ck = cos(th), sk = sin(th);
+    /* direction uniform in the acceptance cone about (ck, sk, 0) */
+    double ct = 1.0 - u0 * (1.0 - cos_max);
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double cph = cos(2.0 * ORC_PI * u1), sph = sin(2.0 * ORC_PI * u1);
+    double d[3] = {ct * ck - st * cph * sk, ct * sk + st * cph * ck, st * sph};
+    if (!(ratio * st < ct)) continue;
+    double x = ratio * st / ct;
+    double pass = (2.0 / ORC_PI) * (acos(x) - x * sqrt(1.0 - x * x));
+    double ang, e1;
+    if (emission) {
+      ang = omega / (4.0 * ORC_PI);
+      e1 = e;
+    } else {
+      double mu_s = d_in[0] * d[0] + d_in[1] * d[1] + d_in[2] * d[2];
+      double eps = 1.0 / (1.0 + (e / ORC_MEC2_KEV) * (1.0 - mu_s));
+      e1 = eps * e;
+      if (e1 < elow) continue;
+      ang = omega * orc_kn_pdf_sr(e, mu_s);
+    }
+    double wt = p_keep * ang * pass * orc_transmission(pb, p, d, e1);
+    int64_t q = (int64_t)llrint(wt * ORC_FD_SCALE);
+    if (q <= 0) continue;
+    double t = (plane - (p[0] * ck + p[1] * sk)) / ct;
+    double qp[3] = {p[0] + t * d[0], p[1] + t * d[1], p[2] + t * d[2]};
+    double a = -qp[0] * sk + qp[1] * ck;
+    double b = qp[2];
+    double r = sqrt(-2.0 * log(u2));
+    a += sigma * (r * cos(2.0 * ORC_PI * u3));
+    b += sigma * (r * sin(2.0 * ORC_PI * u3));
+    double fu = floor(a / pb->bin_mm + 0.5 * pb->n_bins_u);
+    double fv = floor(b / pb->bin_mm + 0.5 * pb->n_bins_v);
+    if (fu < 0.0 || fu >= pb->n_bins_u || fv < 0.0 || fv >= pb->n_bins_v) continue;
+    int32_t row = (int32_t)(((int64_t)k * pb->n_bins_v + (int64_t)fv) * pb->n_bins_u + (int64_t)fu);
+    emit(ctx, row, q);
+  }
+}
+
 /* Follow history h to its end.  Fills rec (if not NULL) and calls emit. */
 static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double mu_maj, orc_record *rec,
-                        orc_emit_fn emit, void *ctx) {
+                        orc_emit_fn emit, orc_emit_w_fn emit_w, void *ctx) {
   orc_stream s;
   stream_init(&s, seed, h);
   orc_counts c = {0, 0, 0, 0};
@@ -334,6 +475,8 @@ static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double
   double d[3] = {st * cos(phi), st * sin(phi), ct};
   double e = pb->e0_kev;
   double elow = e_low(pb);
+  int fd = pb->forced_detection && emit_w;
+  if (fd) fd_point(pb, seed, h, 0u, p, d, e, 1.0, 1, emit_w, ctx);
   int fate;
   for (;;) {
     int m;
@@ -341,6 +484,8 @@ static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double
     int r = woodcock_flight(pb, &s, p, d, e, mu_maj, &c, &m, &mu);
     if (r == 2) { fate = ORC_FATE_CAP; break; }
     if (r == 1) { fate = ORC_FATE_ESCAPE; break; }
+    if (fd && !pb->primary_only)
+      fd_point(pb, seed, h, c.n_real, p, d, e, 1.0 - mu_photo(pb, m, e) / mu, 0, emit_w, ctx);
     if (draw(&s) * mu < mu_photo(pb, m, e)) { fate = ORC_FATE_ABSORBED; break; }
     double mu_c, eps;
     if (compton_sample(&s, e, &mu_c, &eps)) { fate = ORC_FATE_CAP; break; }
@@ -357,7 +502,8 @@ static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double
   }
   /* Sec. 5.3 (dual-matrix OS): the back-projection matrix models attenuation
    * and detector blur only, i.e. photons that reach the camera unscattered */
-  if (fate == ORC_FATE_ESCAPE && !(pb->primary_only && c.n_compton > 0)) detect(pb, &s, p, d, emit, ctx);
+  if (!pb->forced_detection && fate == ORC_FATE_ESCAPE && !(pb->primary_only && c.n_compton > 0))
+    detect(pb, &s, p, d, emit, ctx);
   if (rec) {
     rec->n_virtual = c.n_virtual;
     rec->n_real = c.n_real;
@@ -387,7 +533,7 @@ int orc_trace(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t cou
     rec_ctx ctx;
     ctx.rec = &out[i];
     memset(&out[i], 0, sizeof(out[i]));
-    run_history(pb, seed, first + i, mu_maj, &out[i], emit_to_record, &ctx);
+    run_history(pb, seed, first + i, mu_maj, &out[i], emit_to_record, NULL, &ctx);
   }
   return 0;
 }
@@ -396,12 +542,13 @@ int orc_trace(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t cou
 typedef struct {
   int32_t *row;
   int64_t *col;
+  int64_t *q; /* forced detection: fixed-point weights */
   int64_t n, cap;
   int64_t current_col;
   int failed;
 } ev_buf;
 
-static void emit_to_buf(void *ctx, int32_t row) {
+static void emit_to_buf_w(void *ctx, int32_t row, int64_t q) {
   ev_buf *b = (ev_buf *)ctx;
   if (b->failed) return;
   if (b->n == b->cap) {
@@ -412,12 +559,18 @@ static void emit_to_buf(void *ctx, int32_t row) {
     int64_t *ncl = (int64_t *)realloc(b->col, (size_t)nc * sizeof(int64_t));
     if (!ncl) { b->failed = 1; return; }
     b->col = ncl;
+    int64_t *nq = (int64_t *)realloc(b->q, (size_t)nc * sizeof(int64_t));
+    if (!nq) { b->failed = 1; return; }
+    b->q = nq;
     b->cap = nc;
   }
   b->row[b->n] = row;
   b->col[b->n] = b->current_col;
+  b->q[b->n] = q;
   b->n += 1;
 }
+
+static void emit_to_buf(void *ctx, int32_t row) { emit_to_buf_w(ctx, row, 1); }
 
 typedef struct {
   const orc_problem *pb;
@@ -434,7 +587,7 @@ static void *worker(void *arg) {
     uint64_t h = w->first + i;
     orc_record rec;
     w->buf.current_col = (int64_t)(h % (uint64_t)n_vox);
-    run_history(w->pb, w->seed, h, w->mu_maj, &rec, emit_to_buf, &w->buf);
+    run_history(w->pb, w->seed, h, w->mu_maj, &rec, emit_to_buf, emit_to_buf_w, &w->buf);
     w->fates[rec.fate] += 1;
   }
   return NULL;
@@ -444,8 +597,8 @@ static void *worker(void *arg) {
  * caller owns *rows/*cols (free with orc_free) holding *n_events events in
  * history order; fates[4] counts ABSORBED, BELOW_WINDOW, ESCAPE, CAP.
  * The result does not depend on n_threads. */
-int orc_run(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t count, int n_threads, int32_t **rows,
-            int64_t **cols, int64_t *n_events, uint64_t fates[4]) {
+int orc_run_w(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t count, int n_threads, int32_t **rows,
+              int64_t **cols, int64_t **qs, int64_t *n_events, uint64_t fates[4]) {
   if (n_threads < 1) n_threads = 1;
   if ((uint64_t)n_threads > count && count > 0) n_threads = (int)count;
   if (count == 0) n_threads = 1;
@@ -466,11 +619,12 @@ int orc_run(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t count
   int failed = 0;
   for (int t = 0; t < n_threads; ++t) { total += args[t].buf.n; failed |= args[t].buf.failed; }
   int32_t *r = NULL;
-  int64_t *cl = NULL;
+  int64_t *cl = NULL, *qq = NULL;
   if (!failed) {
     r = (int32_t *)malloc((size_t)(total ? total : 1) * sizeof(int32_t));
     cl = (int64_t *)malloc((size_t)(total ? total : 1) * sizeof(int64_t));
-    if (!r || !cl) failed = 1;
+    qq = (int64_t *)malloc((size_t)(total ? total : 1) * sizeof(int64_t));
+    if (!r || !cl || !qq) failed = 1;
   }
   int64_t off = 0;
   for (int t = 0; t < 4; ++t) fates[t] = 0;
@@ -478,19 +632,28 @@ int orc_run(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t count
     if (!failed && args[t].buf.n) {
       memcpy(r + off, args[t].buf.row, (size_t)args[t].buf.n * sizeof(int32_t));
       memcpy(cl + off, args[t].buf.col, (size_t)args[t].buf.n * sizeof(int64_t));
+      memcpy(qq + off, args[t].buf.q, (size_t)args[t].buf.n * sizeof(int64_t));
       off += args[t].buf.n;
     }
     for (int f = 0; f < 4; ++f) fates[f] += args[t].fates[f];
     free(args[t].buf.row);
     free(args[t].buf.col);
+    free(args[t].buf.q);
   }
   free(args);
   free(th);
-  if (failed) { free(r); free(cl); return -2; }
+  if (failed) { free(r); free(cl); free(qq); return -2; }
   *rows = r;
   *cols = cl;
+  if (qs) *qs = qq; else free(qq);
   *n_events = total;
   return 0;
+}
+
+/* Analog events only (no weights): as orc_run_w without the weights. */
+int orc_run(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t count, int n_threads, int32_t **rows,
+            int64_t **cols, int64_t *n_events, uint64_t fates[4]) {
+  return orc_run_w(pb, seed, first, count, n_threads, rows, cols, NULL, n_events, fates);
 }
 
 void orc_free(void *p) { free(p); }
@@ -560,5 +723,26 @@ int orc_detect(const orc_problem *pb, uint64_t seed, uint64_t h, const double p[
   stream_init(&s, seed, h);
   det_ctx ctx = {rows, max_rows, 0};
   detect(pb, &s, p, d, emit_to_det, &ctx);
+  return ctx.n;
+}
+
+/* Forced copies of one interaction (R7), for the pins: writes up to
+ * max_rows (row, q) pairs and returns how many there were. */
+typedef struct {
+  int32_t *rows;
+  int64_t *qs;
+  int max_rows, n;
+} fdp_ctx;
+
+static void emit_to_fdp(void *ctx, int32_t row, int64_t q) {
+  fdp_ctx *c = (fdp_ctx *)ctx;
+  if (c->n < c->max_rows) { c->rows[c->n] = row; c->qs[c->n] = q; }
+  c->n += 1;
+}
+
+int orc_fd_point(const orc_problem *pb, uint64_t seed, uint64_t h, uint32_t n, const double p[3], const double d_in[3],
+                 double e_kev, double p_keep, int emission, int32_t *rows, int64_t *qs, int max_rows) {
+  fdp_ctx ctx = {rows, qs, max_rows, 0};
+  fd_point(pb, seed, h, n, p, d_in, e_kev, p_keep, emission, emit_to_fdp, &ctx);
   return ctx.n;
 }
