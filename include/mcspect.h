@@ -52,6 +52,25 @@ extern "C" {
 /* what the transport tallies */
 #define MC_TALLY_ALL 0
 #define MC_TALLY_PRIMARY 1
+/* Flag, or-ed with either of the above: forced detection (the paper's
+ * variance-reduction section, "forced detection").  Instead of detecting
+ * the photon where it escapes, a weighted copy is forced to every view at
+ * each interaction location -- the emission point and every real
+ * collision (with MC_TALLY_PRIMARY: the emission point only).  The copy's
+ * direction is uniform in the collimator's acceptance cone about the view's
+ * normal, drawn from its own Philox block (counter (k, 1 + n, h_lo, h_hi)
+ * for view k and interaction n of history h); its weight is the
+ * probability of not being absorbed at the collision (1 - mu_pe/mu; 1 at
+ * emission) times the angular probability of that direction (Omega/(4 pi)
+ * at emission, Omega times the Klein-Nishina density per steradian at a
+ * collision, 0 below the window) times the collimator's open fraction f(x)
+ * times the exact transmission along the ray to the grid boundary; it is
+ * binned like an analog detection.  Weights are tallied in fixed point,
+ * q = rint(w 2^48), and summed as integers, so a build's matrix does not
+ * depend on event order.  The result is a weighted system (entries are
+ * weight sums, float values only); builds are limited to < 2^32 weighted
+ * events (about 2.4e7 histories at 120 views). */
+#define MC_TALLY_FORCED 2
 
 /* storage type of matrix values used by the projectors */
 #define MC_VAL_F32 0
@@ -98,7 +117,8 @@ typedef struct mc_geometry {
   int32_t precision; /* MC_FP32 or MC_FP64 */
   int32_t tally;     /* MC_TALLY_ALL, or MC_TALLY_PRIMARY: only photons that
                         reach the camera unscattered (the attenuation + blur
-                        matrix of dual-matrix OS, Sec. 5.3) */
+                        matrix of dual-matrix OS, Sec. 5.3); either may be
+                        or-ed with MC_TALLY_FORCED */
 } mc_geometry;
 
 typedef struct mc_system mc_system; /* opaque, device resident */
@@ -117,6 +137,9 @@ typedef struct mc_system_info {
   double build_ms_detect;    /* ... of the collimator/detector kernel */
   int32_t spmv_fwd, spmv_bwd; /* projector kernels: 0 = streaming tiles,
                                  else lanes per row (column) group */
+  int32_t weighted;           /* 1: entries are summed forced-detection
+                                 weights (counts = weighted events per entry) */
+  int32_t pad;
 } mc_system_info;
 
 /* Per-history trace (verification): 48 bytes, this exact layout. */
@@ -166,6 +189,24 @@ MC_API int mc_build_system_range(const mc_phantom *phantom, const mc_geometry *g
  * Duplicates add.  Errors: MC_EINVAL for an index out of range. */
 MC_API int mc_system_from_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_host, const int32_t *cols_host,
                           int64_t n_events, uint64_t first, uint64_t count, void *stream, mc_system **out);
+
+/* Weighted matrix from an explicit list of forced-detection events (row j,
+ * column v, fixed-point weight q = rint(w 2^48)), e.g. tallies made
+ * elsewhere (paper's variance-reduction section, forced detection; see
+ * MC_TALLY_FORCED).  Weights of equal (j, v) add as exact integers; n_v is
+ * that of the history range [first, first+count).  The system is weighted:
+ * float values only, no ordered subsets.  Errors: MC_EINVAL for an index out
+ * of range or >= 2^32 events. */
+MC_API int mc_system_from_weighted_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_host,
+                                          const int32_t *cols_host, const uint64_t *weights_host, int64_t n_events,
+                                          uint64_t first, uint64_t count, void *stream, mc_system **out);
+
+/* The entries of the tally matrix as doubles, in the CSC and CSR orders of
+ * the exports below (either pointer may be NULL): the counts C_jv, or for a
+ * weighted system the weight sums q * 2^-48 (exact).  nnz values each.
+ * Synchronises `stream`. */
+MC_API int mc_system_export_values(const mc_system *sys, double *csc_values_host, double *csr_values_host,
+                                   void *stream);
 
 /* Release a system and its device memory (NULL is accepted). */
 MC_API int mc_system_free(mc_system *sys);

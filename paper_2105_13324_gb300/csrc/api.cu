@@ -125,7 +125,10 @@ static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
     return MC_EINVAL;
   }
   if (g->precision != MC_FP32 && g->precision != MC_FP64) { set_error("precision must be MC_FP32 or MC_FP64"); return MC_EINVAL; }
-  if (g->tally != MC_TALLY_ALL && g->tally != MC_TALLY_PRIMARY) { set_error("tally must be MC_TALLY_ALL or MC_TALLY_PRIMARY"); return MC_EINVAL; }
+  if (g->tally < 0 || g->tally > (MC_TALLY_PRIMARY | MC_TALLY_FORCED)) {
+    set_error("tally must be MC_TALLY_ALL or MC_TALLY_PRIMARY, optionally with MC_TALLY_FORCED");
+    return MC_EINVAL;
+  }
   if (ph) {
     const double hx = 0.5 * ph->nx * ph->voxel_mm, hy = 0.5 * ph->ny * ph->voxel_mm;
     if (!(g->radius_mm > std::sqrt(hx * hx + hy * hy))) {
@@ -164,7 +167,9 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
   ts.hole_len = g->hole_len_mm; ts.hole_diam = g->hole_diam_mm; ts.fwhm = g->fwhm_mm;
   ts.e0 = g->e0_kev; ts.window = g->window_frac; ts.photo_k = g->photo_k;
   ts.precision = g->precision;
-  ts.primary_only = g->tally == MC_TALLY_PRIMARY ? 1 : 0;
+  ts.primary_only = (g->tally & MC_TALLY_PRIMARY) ? 1 : 0;
+  ts.forced = (g->tally & MC_TALLY_FORCED) ? 1 : 0;
+  ts.weights = nullptr;
   const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
   MCS_TRY(pl.material.alloc(nv, s));
   MCS_CUDA(cudaMemcpyAsync(pl.material.p, ph->material_host, nv, cudaMemcpyHostToDevice, s));
@@ -269,18 +274,23 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   // headroom.  Queue capacity: an isotropic photon has |d_z| below the
   // collimator's acceptance bound with probability ~w_max.  Both are rerun
   // with the exact sizes if they overflow (transport is deterministic).
-  const uint64_t kChunk = 1ull << 27;
+  // Forced detection: chunks of 2^20 histories; the queue holds interaction
+  // locations (one emission + the real collisions, ~2-3 per history), and
+  // each location gives at most one weighted event per view.
+  const bool forced = ts.forced != 0;
+  const uint64_t kChunk = forced ? (1ull << 20) : (1ull << 27);
   const uint64_t n_chunks = (count + kChunk - 1) / kChunk;
   const uint64_t chunk_max = count < kChunk ? count : kChunk;
   const double tan_max = ts.hole_diam / ts.hole_len;
   const double acc = tan_max * tan_max / 16.0;
-  double est = (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
+  double est = forced ? (double)count * (double)ts.n_views * 2.0 + 65536.0
+                      : (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
   if (est > 4.0e9) est = 4.0e9;
   const double w_max = tan_max / std::sqrt(1.0 + tan_max * tan_max) * 1.02 + 1e-6;
-  double est_q = (double)chunk_max * w_max * 1.1 + 65536.0;
-  if (est_q > (double)chunk_max) est_q = (double)chunk_max;
+  double est_q = forced ? (double)chunk_max * 3.0 + 65536.0 : (double)chunk_max * w_max * 1.1 + 65536.0;
+  if (!forced && est_q > (double)chunk_max) est_q = (double)chunk_max;
   unsigned long long cap = (unsigned long long)est, cap_q = (unsigned long long)est_q;
-  DevBuf events, ctr, esc;
+  DevBuf events, ctr, esc, weights;
   std::vector<cudaEvent_t> evs(3 * n_chunks + 1, nullptr);
   struct EvGuard {
     std::vector<cudaEvent_t> &v;
@@ -291,9 +301,10 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   cudaEvent_t e_end = evs.back();
   if ((rc = ctr.alloc(kCounters * sizeof(unsigned long long), s))) return fail(rc);
   unsigned long long hctr[kCounters];
-  const size_t qb = escape_rec_bytes(ts.precision);
+  const size_t qb = forced ? fd_rec_bytes(ts.precision) : escape_rec_bytes(ts.precision);
   for (int attempt = 0; attempt < 3; ++attempt) {
     if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
+    if (forced && (rc = weights.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
     if ((rc = esc.alloc(cap_q * qb, s))) return fail(rc);
     if (cudaMemsetAsync(ctr.p, 0, kCounters * sizeof(unsigned long long), s) != cudaSuccess) {
       set_error("cudaMemsetAsync failed");
@@ -307,6 +318,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     ts.esc_capacity = cap_q;
     ts.esc_cursor = ctr.as<unsigned long long>() + 5;
     ts.records = nullptr;
+    ts.weights = forced ? weights.as<unsigned long long>() : nullptr;
     for (uint64_t c = 0; c < n_chunks; ++c) {
       ts.first = first + c * kChunk;
       ts.count = (c + 1 < n_chunks) ? kChunk : count - c * kChunk;
@@ -350,8 +362,9 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   esc.release();
   sys->n_events = (int64_t)hctr[0];
   for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
-  rc = assemble_system(sys, events, sys->n_events, s);
+  rc = assemble_system(sys, events, sys->n_events, s, forced ? weights.as<uint64_t>() : nullptr);
   if (rc) return fail(rc);
+  weights.release();
   if ((rc = finish_system(sys, s))) return fail(rc);
   cudaEventRecord(e_end, s);
   cudaEventSynchronize(e_end);
@@ -469,6 +482,90 @@ int mc_system_from_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_ho
   return MC_OK;
 }
 
+int mc_system_from_weighted_events(int64_t n_rows, int64_t n_cols, const int32_t *rows_host, const int32_t *cols_host,
+                                   const uint64_t *weights_host, int64_t n_events, uint64_t first, uint64_t count,
+                                   void *stream, mc_system **out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return MC_EINVAL; }
+  *out = nullptr;
+  if (n_rows < 1 || n_cols < 1 || n_rows >= (1ll << 31) || n_cols >= (1ll << 31) || n_events < 0 ||
+      n_events >= 0xFFFFFFFFll) {
+    set_error("sizes out of range");
+    return MC_EINVAL;
+  }
+  if (n_events > 0 && (!rows_host || !cols_host || !weights_host)) { set_error("event arrays are NULL"); return MC_EINVAL; }
+  for (int64_t i = 0; i < n_events; ++i) {
+    if (rows_host[i] < 0 || rows_host[i] >= n_rows || cols_host[i] < 0 || cols_host[i] >= n_cols) {
+      set_error("event %lld (%d, %d) out of range", (long long)i, rows_host[i], cols_host[i]);
+      return MC_EINVAL;
+    }
+  }
+  cudaStream_t s = API_STREAM(stream);
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete sys; return rc; };
+  sys->n_rows = n_rows;
+  sys->n_cols = n_cols;
+  sys->first = first;
+  sys->count = count;
+  sys->n_events = n_events;
+  DevBuf keys, r, c, w;
+  int rc;
+  const size_t nb = (size_t)(n_events > 0 ? n_events : 1);
+  if ((rc = keys.alloc(nb * 8, s)) || (rc = r.alloc(nb * 4, s)) || (rc = c.alloc(nb * 4, s)) ||
+      (rc = w.alloc(nb * 8, s)))
+    return fail(rc);
+  if (n_events > 0) {
+    if (cudaMemcpyAsync(r.p, rows_host, n_events * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c.p, cols_host, n_events * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w.p, weights_host, n_events * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      set_error("event upload failed");
+      return fail(MC_ECUDA);
+    }
+    int g = (int)((n_events + 255) / 256);
+    if (g > 65535) g = 65535;
+    count_launch(); events_to_keys_kernel<<<g, 256, 0, s>>>(r.as<int32_t>(), c.as<int32_t>(), n_events, (uint64_t)n_rows,
+                                            keys.as<unsigned long long>());
+    if (cudaGetLastError() != cudaSuccess) { set_error("key kernel launch failed"); return fail(MC_ECUDA); }
+  }
+  r.release();
+  c.release();
+  if ((rc = assemble_system(sys, keys, n_events, s, w.as<uint64_t>()))) return fail(rc);
+  w.release();
+  if ((rc = finish_system(sys, s))) return fail(rc);
+  *out = sys;
+  return MC_OK;
+}
+
+__global__ void entries_to_f64_kernel(const uint32_t *cnt, const uint64_t *wq, int64_t n, double *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = wq ? (double)wq[i] * (1.0 / kFdScale) : (double)cnt[i];
+}
+
+int mc_system_export_values(const mc_system *sys, double *csc_values_host, double *csr_values_host, void *stream) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  if (sys->nnz == 0) return MC_OK;
+  cudaStream_t s = API_STREAM(stream);
+  DevBuf tmp;
+  MCS_TRY(tmp.alloc((size_t)sys->nnz * sizeof(double), s));
+  int g = (int)((sys->nnz + 255) / 256);
+  if (g > 65535) g = 65535;
+  for (int side = 0; side < 2; ++side) {
+    double *dst = side == 0 ? csc_values_host : csr_values_host;
+    if (!dst) continue;
+    const DevBuf &cnt = side == 0 ? sys->csc_cnt : sys->csr_cnt;
+    const DevBuf &wq = side == 0 ? sys->csc_wq : sys->csr_wq;
+    count_launch();
+    entries_to_f64_kernel<<<g, 256, 0, s>>>(cnt.as<uint32_t>(), sys->weighted ? wq.as<uint64_t>() : nullptr, sys->nnz,
+                                            tmp.as<double>());
+    MCS_CUDA(cudaGetLastError());
+    MCS_CUDA(cudaMemcpyAsync(dst, tmp.p, (size_t)sys->nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
 int mc_system_free(mc_system *sys) {
   clear_error();
   if (!sys) return MC_OK;
@@ -493,6 +590,7 @@ int mc_system_info_get(const mc_system *sys, mc_system_info *info) {
   info->build_ms_detect = sys->ms_detect;
   info->spmv_fwd = sys->n_csr_blocks > 0 ? 0 : sys->spmv_group_fwd;
   info->spmv_bwd = sys->n_csc_blocks > 0 ? 0 : sys->spmv_group_bwd;
+  info->weighted = sys->weighted ? 1 : 0;
   return MC_OK;
 }
 
@@ -603,6 +701,7 @@ int mc_system_subset(const mc_system *parent, int64_t rows_per_view, int32_t n_s
   if (!parent || !out) { set_error("NULL argument"); return MC_EINVAL; }
   *out = nullptr;
   if (parent->row_map.p) { set_error("the parent is itself a subset"); return MC_EINVAL; }
+  if (parent->weighted) { set_error("ordered subsets of weighted (forced-detection) systems are not supported"); return MC_EINVAL; }
   if (rows_per_view < 1 || parent->n_rows % rows_per_view != 0) {
     set_error("rows_per_view must divide the %lld rows", (long long)parent->n_rows);
     return MC_EINVAL;
@@ -730,6 +829,7 @@ int mc_trace_histories(const mc_phantom *phantom, const mc_geometry *geometry, u
   MCS_TRY(check_phantom(phantom));
   MCS_TRY(check_geometry(geometry, phantom));
   if (count > 0 && !out_host) { set_error("out_host is NULL"); return MC_EINVAL; }
+  if (geometry->tally & MC_TALLY_FORCED) { set_error("per-history traces are analog only (no MC_TALLY_FORCED)"); return MC_EINVAL; }
   if (count == 0) return MC_OK;
   cudaStream_t s = nullptr;
   mc_plan pl;

@@ -281,6 +281,45 @@ __global__ void column_sums_kernel(const uint32_t *col_ptr, const uint32_t *cnt,
   if ((threadIdx.x & 31) == 0 && mymax) atomicMax(max_count, mymax);
 }
 
+// Weighted tallies (forced detection): the weight sum of each run of equal
+// keys, wsum[u] = sum of w[perm[e]] over the run's sorted positions e, as an
+// exact 64-bit integer sum (the weights are fixed point).
+__global__ void iota_kernel(uint32_t *out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)i;
+}
+
+__global__ void run_weights_kernel(const uint32_t *upos, const uint32_t *ucnt, int64_t nu, const uint32_t *perm,
+                                   const uint64_t *w, uint64_t *wsum) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t acc = 0;
+    const uint32_t b = upos[u], e = b + ucnt[u];
+    for (uint32_t k = b; k < e; ++k) acc += w[perm[k]];
+    wsum[u] = acc;
+  }
+}
+
+// out_cnt[i] = cnt[perm[i]], out_w[i] = w[perm[i]]
+__global__ void gather_entries_kernel(const uint32_t *perm, int64_t n, const uint32_t *cnt, const uint64_t *w,
+                                      uint32_t *out_cnt, uint64_t *out_w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = perm[i];
+    out_cnt[i] = cnt[k];
+    out_w[i] = w[k];
+  }
+}
+
+// S_v = sum over column v of the fixed-point weights, in column order
+__global__ void column_weight_sums_kernel(const uint32_t *col_ptr, const uint64_t *wq, int64_t n_cols, double *colsum,
+                                          float *inv_colsum) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_cols; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) acc += (double)wq[k] * (1.0 / kFdScale);
+    colsum[v] = acc;
+    inv_colsum[v] = acc > 0.0 ? (float)(1.0 / acc) : 0.0f;
+  }
+}
+
 static int grid_for(int64_t n, int threads = 256) {
   int64_t g = (n + threads - 1) / threads;
   const int64_t cap = (int64_t)device_sm_count() * 32;
@@ -294,7 +333,7 @@ static int bits_for(uint64_t range) {
   return b;
 }
 
-int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
+int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, const uint64_t *weights) {
   const uint64_t M = (uint64_t)sys->n_rows, N = (uint64_t)sys->n_cols;
   // n_v and 1/n_v
   MCS_TRY(sys->n_v.alloc(N * sizeof(uint32_t), s));
@@ -303,12 +342,23 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
                                                                    sys->inv_n.as<float>());
   MCS_LAUNCHED();
 
-  // 1. sort events by (v, j)
-  DevBuf alt;
+  // 1. sort events by (v, j); weighted: with the event index as payload
+  sys->weighted = weights != nullptr;
+  DevBuf alt, perm, perm_alt, wsum;
   MCS_TRY(alt.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint64_t), s));
+  if (weights) {
+    MCS_TRY(perm.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t), s));
+    MCS_TRY(perm_alt.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t), s));
+    if (n > 0) {
+      count_launch(); iota_kernel<<<grid_for(n), 256, 0, s>>>(perm.as<uint32_t>(), n);
+      MCS_LAUNCHED();
+    }
+  }
   bool in_alt = false;
-  MCS_TRY(radix_sort_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), nullptr, nullptr, n, bits_for(M * N - 1), &in_alt, s));
+  MCS_TRY(radix_sort_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), weights ? perm.as<uint32_t>() : nullptr,
+                         weights ? perm_alt.as<uint32_t>() : nullptr, n, bits_for(M * N - 1), &in_alt, s));
   const uint64_t *sorted = in_alt ? alt.as<uint64_t>() : keys.as<uint64_t>();
+  const uint32_t *sorted_perm = weights ? (in_alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>()) : nullptr;
 
   // 2. run-length encode
   int64_t nu = 0;
@@ -333,8 +383,17 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
     MCS_LAUNCHED();
     count_launch(); run_lengths_kernel<<<grid_for(nu), 256, 0, s>>>(upos.as<uint32_t>(), nu, n, ucnt.as<uint32_t>());
     MCS_LAUNCHED();
+    if (weights) {
+      MCS_TRY(wsum.alloc(nu * sizeof(uint64_t), s));
+      count_launch();
+      run_weights_kernel<<<grid_for(nu), 256, 0, s>>>(upos.as<uint32_t>(), ucnt.as<uint32_t>(), nu, sorted_perm,
+                                                      weights, wsum.as<uint64_t>());
+      MCS_LAUNCHED();
+    }
   }
   alt.release();
+  perm.release();
+  perm_alt.release();
   keys.release();
   sys->nnz = nu;
 
@@ -354,6 +413,10 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
       MCS_CUDA(cudaMemcpyAsync(sys->csc_cnt.p, ucnt.p, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
     MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), (int64_t)N + 1, s));
+    if (weights) {
+      MCS_TRY(sys->csc_wq.alloc(nnz_b * sizeof(uint64_t), s));
+      if (nu > 0) MCS_CUDA(cudaMemcpyAsync(sys->csc_wq.p, wsum.p, nu * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    }
   }
 
   // 4. CSR: sort (j*N + v, count) pairs, then row_ptr from a histogram of j
@@ -370,15 +433,33 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
       MCS_TRY(tcnt_alt.alloc(nu * sizeof(uint32_t), s));
       count_launch(); transpose_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, N, tkeys.as<uint64_t>());
       MCS_LAUNCHED();
+      // payload: the counts, or (weighted) the CSC position of each entry
+      DevBuf tperm;
+      if (weights) {
+        MCS_TRY(tperm.alloc(nu * sizeof(uint32_t), s));
+        count_launch(); iota_kernel<<<grid_for(nu), 256, 0, s>>>(tperm.as<uint32_t>(), nu);
+        MCS_LAUNCHED();
+      }
+      uint32_t *payload = weights ? tperm.as<uint32_t>() : ucnt.as<uint32_t>();
       bool talt = false;
-      MCS_TRY(radix_sort_u64(tkeys.as<uint64_t>(), tkeys_alt.as<uint64_t>(), ucnt.as<uint32_t>(),
+      MCS_TRY(radix_sort_u64(tkeys.as<uint64_t>(), tkeys_alt.as<uint64_t>(), payload,
                              tcnt_alt.as<uint32_t>(), nu, bits_for(M * N - 1), &talt, s));
       const uint64_t *tk = talt ? tkeys_alt.as<uint64_t>() : tkeys.as<uint64_t>();
-      const uint32_t *tc = talt ? tcnt_alt.as<uint32_t>() : ucnt.as<uint32_t>();
+      const uint32_t *tc = talt ? tcnt_alt.as<uint32_t>() : payload;
       count_launch(); split_keys_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, N, nullptr, sys->col_idx.as<uint32_t>(),
                                                      hist.as<uint32_t>());
       MCS_LAUNCHED();
-      MCS_CUDA(cudaMemcpyAsync(sys->csr_cnt.p, tc, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+      if (weights) {
+        MCS_TRY(sys->csr_wq.alloc(nu * sizeof(uint64_t), s));
+        count_launch();
+        gather_entries_kernel<<<grid_for(nu), 256, 0, s>>>(tc, nu, ucnt.as<uint32_t>(), wsum.as<uint64_t>(),
+                                                           sys->csr_cnt.as<uint32_t>(), sys->csr_wq.as<uint64_t>());
+        MCS_LAUNCHED();
+      } else {
+        MCS_CUDA(cudaMemcpyAsync(sys->csr_cnt.p, tc, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+      }
+    } else if (weights) {
+      MCS_TRY(sys->csr_wq.alloc(sizeof(uint64_t), s));
     }
     MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->row_ptr.as<uint32_t>(), (int64_t)M + 1, s));
   }
@@ -394,6 +475,15 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s) {
                                                             (int64_t)N, sys->colsum.as<double>(),
                                                             sys->inv_colsum.as<float>(), mx.as<unsigned int>());
     MCS_LAUNCHED();
+    if (weights) {
+      // S_v from the weights (the kernel above gave the largest event count)
+      count_launch();
+      column_weight_sums_kernel<<<grid_for((int64_t)N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(),
+                                                                     sys->csc_wq.as<uint64_t>(), (int64_t)N,
+                                                                     sys->colsum.as<double>(),
+                                                                     sys->inv_colsum.as<float>());
+      MCS_LAUNCHED();
+    }
     unsigned int mxh = 0;
     MCS_CUDA(cudaMemcpyAsync(&mxh, mx.p, sizeof(mxh), cudaMemcpyDeviceToHost, s));
     MCS_CUDA(cudaStreamSynchronize(s));
@@ -417,6 +507,12 @@ template <typename V> __global__ void convert_counts_kernel(const uint32_t *cnt,
     out[i] = from_count<V>(cnt[i]);
 }
 
+// weighted systems: the fixed-point weight sums as float
+__global__ void convert_weights_kernel(const uint64_t *wq, int64_t n, float *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)((double)wq[i] * (1.0 / kFdScale));
+}
+
 int make_values(mc_system *sys, cudaStream_t s) {
   const int64_t nnz = sys->nnz;
   const size_t es = sys->value_type == MC_VAL_F32 ? 4 : 2;
@@ -425,7 +521,11 @@ int make_values(mc_system *sys, cudaStream_t s) {
   MCS_TRY(sys->csc_val.alloc(bytes, s));
   if (nnz == 0) return MC_OK;
   const int g = grid_for(nnz);
-  if (sys->value_type == MC_VAL_F32) {
+  if (sys->weighted) {
+    if (sys->value_type != MC_VAL_F32) { set_error("weighted systems keep float values"); return MC_EINVAL; }
+    count_launch(); convert_weights_kernel<<<g, 256, 0, s>>>(sys->csr_wq.as<uint64_t>(), nnz, sys->csr_val.as<float>());
+    count_launch(); convert_weights_kernel<<<g, 256, 0, s>>>(sys->csc_wq.as<uint64_t>(), nnz, sys->csc_val.as<float>());
+  } else if (sys->value_type == MC_VAL_F32) {
     count_launch(); convert_counts_kernel<float><<<g, 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), nnz, sys->csr_val.as<float>());
     count_launch(); convert_counts_kernel<float><<<g, 256, 0, s>>>(sys->csc_cnt.as<uint32_t>(), nnz, sys->csc_val.as<float>());
   } else if (sys->value_type == MC_VAL_F16) {

@@ -116,6 +116,11 @@ struct mc_system {
   mcs::DevBuf csr_blocks, csc_blocks;  // u32 [n_blocks + 1] first row / column of each tile
   int64_t n_csr_blocks = 0, n_csc_blocks = 0;
   bool warp_rows_fwd = false, warp_rows_bwd = false;
+  // forced detection: the entries are summed event weights instead of
+  // counts, in fixed point (q * 2^-48); the counts above are then the
+  // number of weighted events per entry
+  bool weighted = false;
+  mcs::DevBuf csr_wq, csc_wq;  // u64 [nnz]
   // ordered subsets: row i of this system is row row_map[i] of its parent
   // (empty for a full system)
   mcs::DevBuf row_map;
@@ -162,7 +167,15 @@ struct TransportSetup {
   cudaEvent_t ev_mid;          // recorded between transport and detection (optional)
   int precision;
   int primary_only;            // tally only unscattered photons
+  int forced;                  // forced detection: weighted copies instead of analog detection
+  unsigned long long *weights; // forced detection: fixed-point weight of each event (else null)
 };
+
+// forced detection: event weights are tallied as q = rint(w * 2^48)
+constexpr double kFdScale = 281474976710656.0;
+
+// bytes of one forced-detection interaction record for a precision
+inline size_t fd_rec_bytes(int precision) { return precision == MC_FP64 ? 80 : 48; }
 
 // bytes of one escape-queue entry for a precision
 inline size_t escape_rec_bytes(int precision) { return precision == MC_FP64 ? 64 : 40; }
@@ -175,7 +188,9 @@ int launch_debug_beam(const TransportSetup &ts, uint64_t n, const double p0[3], 
 
 // Assembly: sorted events -> CSR + CSC + n_v + column sums.  `keys` holds
 // n keys (v*M + j) and is overwritten.
-int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s);
+// `weights` (device, optional): fixed-point weight of each event; the
+// entries are then the weight sums (the system is marked weighted).
+int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, const uint64_t *weights = nullptr);
 
 // Projector value arrays for sys->value_type.
 int make_values(mc_system *sys, cudaStream_t s);

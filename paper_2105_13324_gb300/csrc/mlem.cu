@@ -844,13 +844,19 @@ extern "C" int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, fl
 namespace mcs {
 
 // q_j = sum_v C_jv x_v / n_v, one thread per row, double accumulation
+// entry k as a double: the count, or (weighted systems) the fixed-point
+// weight sum
+__device__ __forceinline__ double entry_f64(const uint32_t *cnt, const uint64_t *wq, uint32_t k) {
+  return wq ? (double)wq[k] * (1.0 / kFdScale) : (double)cnt[k];
+}
+
 __global__ void forward_f64_kernel(const uint32_t *row_ptr, const uint32_t *col, const uint32_t *cnt,
-                                   const uint32_t *n_v, const double *x, int64_t m, double *q) {
+                                   const uint64_t *wq, const uint32_t *n_v, const double *x, int64_t m, double *q) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (uint32_t k = row_ptr[j]; k < row_ptr[j + 1]; ++k) {
       const uint32_t v = col[k];
-      acc += (double)cnt[k] * (x[v] / (double)n_v[v]);
+      acc += entry_f64(cnt, wq, k) * (x[v] / (double)n_v[v]);
     }
     q[j] = acc;
   }
@@ -858,10 +864,10 @@ __global__ void forward_f64_kernel(const uint32_t *row_ptr, const uint32_t *col,
 
 // b_v = (1/n_v) sum_j C_jv r_j
 __global__ void back_f64_kernel(const uint32_t *col_ptr, const uint32_t *row, const uint32_t *cnt,
-                                const uint32_t *n_v, const double *r, int64_t n, double *b) {
+                                const uint64_t *wq, const uint32_t *n_v, const double *r, int64_t n, double *b) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) acc += (double)cnt[k] * r[row[k]];
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) acc += entry_f64(cnt, wq, k) * r[row[k]];
     b[v] = n_v[v] ? acc / (double)n_v[v] : 0.0;
   }
 }
@@ -910,7 +916,7 @@ int project_f64(const mc_system *sys, const double *x, double *q, cudaStream_t s
     count_launch();
     forward_f64_kernel<<<grid_stride_blocks(sys->n_rows), 256, 0, s>>>(
         sys->row_ptr.as<uint32_t>(), sys->col_idx.as<uint32_t>(), sys->csr_cnt.as<uint32_t>(),
-        sys->n_v.as<uint32_t>(), x, sys->n_rows, q);
+        sys->weighted ? sys->csr_wq.as<uint64_t>() : nullptr, sys->n_v.as<uint32_t>(), x, sys->n_rows, q);
   }
   MCS_LAUNCHED();
   return MC_OK;
@@ -921,7 +927,7 @@ int backproject_f64(const mc_system *sys, const double *r, double *b, cudaStream
     count_launch();
     back_f64_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(
         sys->col_ptr.as<uint32_t>(), sys->row_idx.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
-        sys->n_v.as<uint32_t>(), r, sys->n_cols, b);
+        sys->weighted ? sys->csc_wq.as<uint64_t>() : nullptr, sys->n_v.as<uint32_t>(), r, sys->n_cols, b);
   }
   MCS_LAUNCHED();
   return MC_OK;

@@ -68,9 +68,12 @@ template <typename T> struct TArgs {
   unsigned long long *cursor;
   unsigned long long *fates;
   mc_history_record *records;
-  void *esc;                        // EscapeRec<T>[esc_capacity]
+  void *esc;                        // EscapeRec<T>[esc_capacity] (forced detection: FdRec<T>)
   unsigned long long esc_capacity;
   unsigned long long *esc_cursor;
+  unsigned long long *weights;      // forced detection: fixed-point event weights
+  T cos_max, omega, omega_4pi;      // acceptance cone: cos of its half-angle, solid angle, / 4 pi
+  T one_m_cos_max;                  // 1 - cos_max (float path: sin^2 from 1 - cos without cancellation)
 };
 
 // An escaping photon that may pass a collimator: its history, the position
@@ -81,6 +84,18 @@ template <typename T> struct EscapeRec {
   T p[3], d[3];
 };
 static_assert(sizeof(EscapeRec<float>) == 40 && sizeof(EscapeRec<double>) == 64, "escape record layout");
+
+// Forced detection: one interaction location of a history -- its emission
+// (n = 0) or its n-th real collision -- with the photon's energy and
+// direction before the interaction and the probability 1 - mu_pe/mu that
+// the photon is not absorbed there (1 at emission).
+template <typename T> struct FdRec {
+  uint64_t h;
+  uint32_t n, pad;
+  T p[3], d[3];
+  T e, keep;
+};
+static_assert(sizeof(FdRec<float>) == 48 && sizeof(FdRec<double>) == 80, "forced-detection record layout");
 
 // Philox4x32-10 with precomputed round keys (Salmon et al., SC'11): each
 // round is two 32x32->64 multiplies and two three-way xors.
@@ -421,7 +436,28 @@ __device__ __forceinline__ void detect(const TArgs<T> &a, KStream &st, T px, T p
   for (int k = 0; k < a.n_views; ++k) try_view<T, TRACE>(a, st, k, px, py, pz, dx, dy, dz, v, sink);
 }
 
-template <typename T, bool TRACE>
+// Queue an interaction location for the forced-detection kernel.
+template <typename T>
+__device__ __forceinline__ void push_fd(const TArgs<T> &a, uint64_t h, uint32_t n, T px, T py, T pz, T dx, T dy,
+                                        T dz, T e, T keep) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(a.esc_cursor, (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  const unsigned long long q = base + g.thread_rank();
+  if (q < a.esc_capacity) {
+    FdRec<T> r;
+    r.h = h; r.n = n; r.pad = 0;
+    r.p[0] = px; r.p[1] = py; r.p[2] = pz;
+    r.d[0] = dx; r.d[1] = dy; r.d[2] = dz;
+    r.e = e; r.keep = keep;
+    static_cast<FdRec<T> *>(a.esc)[q] = r;
+  }
+}
+
+// FD: forced-detection mode -- instead of queueing escapes for analog
+// detection, queue every interaction location (emission, real collisions).
+template <typename T, bool TRACE, bool FD = false>
 __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_constant__ TArgs<T> a) {
   __shared__ T s_c0[256], s_c1[256], s_c2[256];
   __shared__ float s_sig[kSigTab];
@@ -495,6 +531,9 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
     }
     int fate = -1;
     if (do_coll && st == S_COLLIDE) {
+      if (FD && !a.primary_only)
+        push_fd<T>(a, a.first + cur_i, n_real, px, py, pz, dx, dy, dz, en.e,
+                   (T)1 - mu_photo<T>(s_c0, s_c1, s_c2, m_col, en) / mu_col);
       // photo-absorption, else a Klein-Nishina scatter, at the pending collision
       rg.ensure(1, a);
       if (uniform<T>(rg.next()) * mu_col < mu_photo<T>(s_c0, s_c1, s_c2, m_col, en)) {
@@ -544,6 +583,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       en = en0;
       steps = n_virtual = n_real = n_compton = 0;
       st = S_FLY;
+      if (FD) push_fd<T>(a, a.first + cur_i, 0u, px, py, pz, dx, dy, dz, en.e, (T)1);
       if (!(a.mu_maj > (T)0)) fate = MC_FATE_ESCAPE;
     }
     if (st == S_FLY && fate < 0) {
@@ -576,7 +616,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       }
     }
     if (fate >= 0) {
-      if (fate == MC_FATE_ESCAPE && fabs(dz) < a.w_max && !(a.primary_only && n_compton > 0)) {
+      if (!FD && fate == MC_FATE_ESCAPE && fabs(dz) < a.w_max && !(a.primary_only && n_compton > 0)) {
         // a view may accept it: queue it for the detection kernel
         cg::coalesced_group g = cg::coalesced_threads();
         unsigned long long base = 0;
@@ -662,6 +702,179 @@ __global__ void __launch_bounds__(256) detect_kernel(const __grid_constant__ TAr
     EventSink sink{a.events, a.cursor, a.capacity, rec};
     detect<T, TRACE>(a, st, r.p[0], r.p[1], r.p[2], r.d[0], r.d[1], r.d[2], v, sink);
     if (TRACE) rec->n_draws = st.n_draws;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forced detection
+// ---------------------------------------------------------------------------
+// Transmission exp(-integral of mu(E) ds) from p along d to the grid
+// boundary: the voxels the ray crosses are visited in order (the next voxel
+// lies across the nearest of the three next faces, ties to the lowest axis)
+// and mu times the length inside each is summed.
+template <typename T>
+__device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T dx, T dy, T dz, T e,
+                                          const T *c0, const T *c1, const T *c2, const float *sig_tab) {
+  Energy<T> en;
+  en.set(e, a, sig_tab);
+  int ix = voxel_index<T>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
+  int iy = voxel_index<T>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
+  int iz = voxel_index<T>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
+  const int sx = dx > (T)0 ? 1 : (dx < (T)0 ? -1 : 0);
+  const int sy = dy > (T)0 ? 1 : (dy < (T)0 ? -1 : 0);
+  const int sz = dz > (T)0 ? 1 : (dz < (T)0 ? -1 : 0);
+  // distance along the ray to the next face on one axis
+  auto face = [&](int i, int s, T half, T p, T d) -> T {
+    if (s == 0) return (T)INFINITY;
+    const T b = -half + (T)(i + (s > 0 ? 1 : 0)) * a.h;
+    return (b - p) / d;
+  };
+  T tx = face(ix, sx, a.hx, px, dx), ty = face(iy, sy, a.hy, py, dy), tz = face(iz, sz, a.hz, pz, dz);
+  T t = (T)0, sum = (T)0;
+  const int max_steps = a.nx + a.ny + a.nz + 3;
+  for (int it = 0; it < max_steps; ++it) {
+    const int m = __ldg(a.mat + ((size_t)iz * a.ny + iy) * a.nx + ix);
+    int ax = 0;
+    T t1 = tx;
+    if (ty < t1) { ax = 1; t1 = ty; }
+    if (tz < t1) { ax = 2; t1 = tz; }
+    if (t1 > t) {
+      sum += mu_total<T>(c0, c1, c2, m, en) * (t1 - t);
+      t = t1;
+    }
+    if (ax == 0) {
+      ix += sx;
+      if (ix < 0 || ix >= a.nx) break;
+      tx = face(ix, sx, a.hx, px, dx);
+    } else if (ax == 1) {
+      iy += sy;
+      if (iy < 0 || iy >= a.ny) break;
+      ty = face(iy, sy, a.hy, py, dy);
+    } else {
+      iz += sz;
+      if (iz < 0 || iz >= a.nz) break;
+      tz = face(iz, sz, a.hz, pz, dz);
+    }
+  }
+  if constexpr (is_dbl<T>()) return exp(-sum);
+  else return __expf(-sum);
+}
+
+// Klein-Nishina angular density of the scattered direction per steradian,
+// (dsigma/dOmega) / sigma_KN, dsigma/dOmega = (r_e^2/2) eps^2 (eps + 1/eps -
+// sin^2 theta), eps = 1/(1 + alpha (1 - cos theta)).
+template <typename T> __device__ __forceinline__ T kn_pdf_sr(T e, T mu, const Energy<T> &en) {
+  if constexpr (is_dbl<T>()) {
+    const double alpha = e / kMec2;
+    const double eps = 1.0 / (1.0 + alpha * (1.0 - mu));
+    const double dsig = 0.5 * kRe * kRe * (eps * eps) * (eps + 1.0 / eps - (1.0 - mu * mu));
+    return dsig / en.sig;
+  } else {
+    const float den = 1.0f + e * (float)(1.0 / kMec2) * (1.0f - mu);
+    const float eps = __fdividef(1.0f, den);
+    const float dsig = (float)(0.5 * kRe * kRe) * (eps * eps) * (eps + den - (1.0f - mu * mu));
+    return dsig / en.sig;
+  }
+}
+
+// The forced copy of record r towards view k: a direction uniform in the
+// collimator's acceptance cone about the view's normal, drawn from the
+// copy's own Philox block (counter (k, 1 + n, h_lo, h_hi)), weighted by
+// the survival at the interaction, the angular probability of that
+// direction, the collimator's open fraction and the transmission to the
+// grid boundary, then binned like an analog detection.
+template <typename T>
+__device__ __forceinline__ void fd_copy(const TArgs<T> &a, const FdRec<T> &r, int k, const T *c0, const T *c1,
+                                        const T *c2, const float *sig_tab) {
+  uint32_t w0 = (uint32_t)k, w1 = 1u + r.n, w2 = (uint32_t)r.h, w3 = (uint32_t)(r.h >> 32);
+  philox_rounds(w0, w1, w2, w3, a.rk);
+  const T u0 = uniform<T>(w0), u1 = uniform<T>(w1), u2 = uniform<T>(w2), u3 = uniform<T>(w3);
+  const T ck = a.view_cs[2 * k], sk = a.view_cs[2 * k + 1];
+  T ct, st;
+  if constexpr (is_dbl<T>()) {
+    ct = 1.0 - u0 * (1.0 - a.cos_max);
+    st = sqrt0<double>(1.0 - ct * ct);
+  } else {
+    // 1 - cos is a few 1e-3 at most: sin^2 = (1 - cos)(1 + cos) keeps float's
+    // relative precision where 1 - cos^2 would cancel
+    const float om = u0 * a.one_m_cos_max;
+    ct = 1.0f - om;
+    st = sqrt0<float>(om * (2.0f - om));
+  }
+  T cph, sph;
+  cos_sin_2pi<T>(u1, cph, sph);
+  const T dx = ct * ck - st * cph * sk, dy = ct * sk + st * cph * ck, dz = st * sph;
+  if (!(a.ratio * st < ct)) return;
+  const T x = a.ratio * st / ct;
+  const T pass = (T)(2.0 / kPi) * (acos(x) - x * sqrt0<T>((T)1 - x * x));
+  T ang, e1;
+  if (r.n == 0) {
+    ang = a.omega_4pi;
+    e1 = r.e;
+  } else {
+    const T mu_s = r.d[0] * dx + r.d[1] * dy + r.d[2] * dz;
+    if constexpr (is_dbl<T>()) {
+      const double eps = 1.0 / (1.0 + (r.e / kMec2) * (1.0 - mu_s));
+      e1 = eps * r.e;
+    } else {
+      e1 = __fdividef(r.e, 1.0f + r.e * (float)(1.0 / kMec2) * (1.0f - mu_s));
+    }
+    if (e1 < a.e_low) return;
+    Energy<T> en;
+    en.set(r.e, a, sig_tab);
+    ang = a.omega * kn_pdf_sr<T>(r.e, mu_s, en);
+  }
+  const T wt = r.keep * ang * pass * transmission<T>(a, r.p[0], r.p[1], r.p[2], dx, dy, dz, e1, c0, c1, c2, sig_tab);
+  const long long q = __double2ll_rn((double)wt * kFdScale);
+  if (q <= 0) return;
+  const T t = (a.plane - (r.p[0] * ck + r.p[1] * sk)) / ct;
+  const T qx = r.p[0] + t * dx, qy = r.p[1] + t * dy, qz = r.p[2] + t * dz;
+  T au = -qx * sk + qy * ck;
+  T bv = qz;
+  T rr;
+  if constexpr (is_dbl<T>()) rr = sqrt(-2.0 * log(u2));
+  else rr = sqrt0<float>(-2.0f * __logf(u2));
+  T cb, sb;
+  cos_sin_2pi<T>(u3, cb, sb);
+  au += a.sigma * (rr * cb);
+  bv += a.sigma * (rr * sb);
+  const T fu = floor(au / a.bin + a.half_bu);
+  const T fv = floor(bv / a.bin + a.half_bv);
+  if (!(fu >= (T)0 && fu < (T)a.bins_u && fv >= (T)0 && fv < (T)a.bins_v)) return;
+  const uint64_t row = ((uint64_t)k * a.bins_v + (uint64_t)fv) * a.bins_u + (uint64_t)fu;
+  const uint64_t v = r.h % a.n_vox;
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(a.cursor, (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  const unsigned long long idx = base + g.thread_rank();
+  if (idx < a.capacity) {
+    a.events[idx] = (unsigned long long)(v * a.n_rows + row);
+    a.weights[idx] = (unsigned long long)q;
+  }
+}
+
+// One thread per (queued interaction, view), views fastest.
+template <typename T>
+__global__ void __launch_bounds__(256) fd_kernel(const __grid_constant__ TArgs<T> a) {
+  __shared__ T s_c0[256], s_c1[256], s_c2[256];
+  __shared__ float s_sig[kSigTab];
+  for (int m = threadIdx.x; m < a.n_mat; m += blockDim.x) {
+    s_c0[m] = a.coef[3 * m];
+    s_c1[m] = a.coef[3 * m + 1];
+    s_c2[m] = a.coef[3 * m + 2];
+  }
+  if (!is_dbl<T>())
+    for (int i = threadIdx.x; i < kSigTab; i += blockDim.x) s_sig[i] = a.sig_tab[i];
+  __syncthreads();
+  const unsigned long long n_q = *a.esc_cursor < a.esc_capacity ? *a.esc_cursor : a.esc_capacity;
+  const unsigned long long total = n_q * (unsigned long long)a.n_views;
+  const FdRec<T> *q = static_cast<const FdRec<T> *>(a.esc);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long ri = i / (unsigned long long)a.n_views;
+    const int k = (int)(i - ri * (unsigned long long)a.n_views);
+    fd_copy<T>(a, q[ri], k, s_c0, s_c1, s_c2, s_sig);
   }
 }
 
@@ -840,6 +1053,13 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.esc = ts.esc;
   a.esc_capacity = ts.esc_capacity;
   a.esc_cursor = ts.esc_cursor;
+  a.weights = ts.weights;
+  const double cos_max = 1.0 / std::sqrt(1.0 + tan_max * tan_max);
+  const double omega = 2.0 * kPi * (1.0 - cos_max);
+  a.cos_max = (T)cos_max;
+  a.omega = (T)omega;
+  a.omega_4pi = (T)(omega / (4.0 * kPi));
+  a.one_m_cos_max = (T)(1.0 - cos_max);
 }
 
 template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStream_t s) {
@@ -848,7 +1068,9 @@ template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStrea
   if (ts.count == 0) return MC_OK;
   const int threads = 256;
   int per_sm = 0;
-  if (ts.records) {
+  if (ts.forced) {
+    MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, transport_kernel<T, false, true>, threads, 0));
+  } else if (ts.records) {
     MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, transport_kernel<T, true>, threads, 0));
   } else {
     MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, transport_kernel<T, false>, threads, 0));
@@ -857,12 +1079,14 @@ template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStrea
   const int64_t full = (int64_t)device_sm_count() * per_sm;
   const int64_t need = (int64_t)((ts.count + threads - 1) / threads);
   const int grid = (int)(need < full ? need : full);
-  if (ts.records) { count_launch(); transport_kernel<T, true><<<grid, threads, 0, s>>>(a); }
+  if (ts.forced) { count_launch(); transport_kernel<T, false, true><<<grid, threads, 0, s>>>(a); }
+  else if (ts.records) { count_launch(); transport_kernel<T, true><<<grid, threads, 0, s>>>(a); }
   else { count_launch(); transport_kernel<T, false><<<grid, threads, 0, s>>>(a); }
   MCS_LAUNCHED();
   if (ts.ev_mid) MCS_CUDA(cudaEventRecord(ts.ev_mid, s));
   const int dgrid = device_sm_count() * 8;
-  if (ts.records) { count_launch(); detect_kernel<T, true><<<dgrid, 256, 0, s>>>(a); }
+  if (ts.forced) { count_launch(); fd_kernel<T><<<dgrid, 256, 0, s>>>(a); }
+  else if (ts.records) { count_launch(); detect_kernel<T, true><<<dgrid, 256, 0, s>>>(a); }
   else { count_launch(); detect_kernel<T, false><<<dgrid, 256, 0, s>>>(a); }
   MCS_LAUNCHED();
   return MC_OK;

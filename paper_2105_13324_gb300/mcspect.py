@@ -23,12 +23,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EFORMAT = 0, -1, -2, -3, -4, -5
 MC_FP32, MC_FP64 = 0, 1
 MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
-MC_TALLY_ALL, MC_TALLY_PRIMARY = 0, 1
+MC_TALLY_ALL, MC_TALLY_PRIMARY, MC_TALLY_FORCED = 0, 1, 2
+FD_SCALE = 2.0 ** 48  # forced-detection weights are tallied as rint(w * 2^48)
 FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 
 # every symbol include/mcspect.h declares
 EXPORTED = (
-    "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events", "mc_system_free",
+    "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events",
+    "mc_system_from_weighted_events", "mc_system_export_values", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
     "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
@@ -73,7 +75,8 @@ class MCSystemInfo(ctypes.Structure):
                 ("n_histories", ctypes.c_uint64), ("fates", ctypes.c_uint64 * 4), ("max_count", ctypes.c_uint32),
                 ("value_type", ctypes.c_int32), ("build_ms_transport", ctypes.c_double),
                 ("build_ms_assembly", ctypes.c_double), ("build_ms_detect", ctypes.c_double),
-                ("spmv_fwd", ctypes.c_int32), ("spmv_bwd", ctypes.c_int32)]
+                ("spmv_fwd", ctypes.c_int32), ("spmv_bwd", ctypes.c_int32), ("weighted", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,6 +101,8 @@ def load(path: str | None = None):
             "mc_build_system": [vp, vp, u64, u64, vp, vp],
             "mc_build_system_range": [vp, vp, u64, u64, u64, vp, vp],
             "mc_system_from_events": [i64, i64, vp, vp, i64, u64, u64, vp, vp],
+            "mc_system_from_weighted_events": [i64, i64, vp, vp, vp, i64, u64, u64, vp, vp],
+            "mc_system_export_values": [vp, vp, vp, vp],
             "mc_system_free": [vp],
             "mc_system_info_get": [vp, vp],
             "mc_system_export_csc": [vp, vp, vp, vp, vp, vp],
@@ -163,7 +168,8 @@ def _dev_ptr(t, dtype=None):
 class _Inputs:
     """C structs for a Phantom + Geometry, keeping NumPy buffers alive."""
 
-    def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int, primary_only: bool = False):
+    def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int, primary_only: bool = False,
+                 forced: bool = False):
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -175,7 +181,8 @@ class _Inputs:
         self.geo = MCGeometry(g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
                               float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
                               float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
-                              int(precision), int(bool(primary_only)))
+                              int(precision),
+                              (MC_TALLY_PRIMARY if primary_only else 0) | (MC_TALLY_FORCED if forced else 0))
 
 
 def _precision(p):
@@ -206,7 +213,7 @@ class System:
                 "fates": [int(v) for v in inf.fates], "max_count": inf.max_count,
                 "value_type": inf.value_type, "build_ms_transport": inf.build_ms_transport,
                 "build_ms_assembly": inf.build_ms_assembly, "build_ms_detect": inf.build_ms_detect,
-                "spmv_fwd": inf.spmv_fwd, "spmv_bwd": inf.spmv_bwd}
+                "spmv_fwd": inf.spmv_fwd, "spmv_bwd": inf.spmv_bwd, "weighted": bool(inf.weighted)}
 
     @property
     def shape(self):
@@ -232,6 +239,15 @@ class System:
                                            _stream_ptr(stream)))
         return rp, ci[:i["nnz"]], cnt[:i["nnz"]]
 
+    def export_values(self, stream=None):
+        """Entries as float64 in the CSC and CSR orders of export_csc /
+        export_csr: counts, or the weight sums of a weighted system."""
+        n = self.info()["nnz"]
+        a = np.zeros(max(n, 1), np.float64)
+        b = np.zeros(max(n, 1), np.float64)
+        _check(load().mc_system_export_values(self.handle, a.ctypes.data, b.ctypes.data, _stream_ptr(stream)))
+        return a[:n], b[:n]
+
     def set_value_type(self, value_type, allow_rounding=False):
         vt = {"f32": MC_VAL_F32, "f16": MC_VAL_F16, "bf16": MC_VAL_BF16}.get(value_type, value_type)
         _check(load().mc_system_set_value_type(self.handle, int(vt), int(bool(allow_rounding))))
@@ -253,8 +269,8 @@ class System:
 class Plan:
     """Owner of an mc_plan handle: phantom + geometry resident on the device."""
 
-    def __init__(self, phantom, geometry, precision="fp32", stream=None, primary_only=False):
-        inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
+    def __init__(self, phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False):
+        inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
         h = ctypes.c_void_p()
         _check(load().mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), _stream_ptr(stream),
                                      ctypes.byref(h)))
@@ -277,8 +293,8 @@ class Plan:
             pass
 
 
-def mc_plan_create(phantom, geometry, precision="fp32", stream=None, primary_only=False) -> Plan:
-    return Plan(phantom, geometry, precision, stream, primary_only)
+def mc_plan_create(phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False) -> Plan:
+    return Plan(phantom, geometry, precision, stream, primary_only, forced)
 
 
 def mc_plan_build(plan: Plan, first: int, count: int, seed: int, stream=None) -> System:
@@ -298,8 +314,8 @@ def mc_kernel_launches() -> int:
 
 
 def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="fp32", stream=None,
-                    primary_only=False) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
+                    primary_only=False, forced=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
     h = ctypes.c_void_p()
     _check(load().mc_build_system(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(n_histories), int(seed),
                                   _stream_ptr(stream), ctypes.byref(h)))
@@ -307,8 +323,8 @@ def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="f
 
 
 def mc_build_system_range(phantom, geometry, first: int, count: int, seed: int, precision="fp32",
-                          stream=None, primary_only=False) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
+                          stream=None, primary_only=False, forced=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
     h = ctypes.c_void_p()
     _check(load().mc_build_system_range(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(first), int(count),
                                         int(seed), _stream_ptr(stream), ctypes.byref(h)))
@@ -323,6 +339,21 @@ def mc_system_from_events(n_rows: int, n_cols: int, rows, cols, first: int, coun
     h = ctypes.c_void_p()
     _check(load().mc_system_from_events(int(n_rows), int(n_cols), r.ctypes.data, c.ctypes.data, int(r.size),
                                         int(first), int(count), _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_system_from_weighted_events(n_rows: int, n_cols: int, rows, cols, weights, first: int, count: int,
+                                   stream=None) -> System:
+    """weights: fixed-point event weights (uint64, w * 2^48 rounded)."""
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    w = np.ascontiguousarray(weights, dtype=np.uint64)
+    if r.shape != c.shape or r.shape != w.shape:
+        raise ValueError("rows, cols and weights differ in length")
+    h = ctypes.c_void_p()
+    _check(load().mc_system_from_weighted_events(int(n_rows), int(n_cols), r.ctypes.data, c.ctypes.data,
+                                                 w.ctypes.data, int(r.size), int(first), int(count),
+                                                 _stream_ptr(stream), ctypes.byref(h)))
     return System(h)
 
 
