@@ -326,6 +326,74 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
     return out
 
 
+def _blocks(q, geometry, b=8):
+    # projection (views x bins_v x bins_u) summed over b x b bins
+    V, bv, bu = geometry.n_views, geometry.n_bins_v, geometry.n_bins_u
+    return q.reshape(V, bv // b, b, bu // b, b).sum(axis=(2, 4)).ravel()
+
+
+def fd_benchmark(mc, w, analog, analog_ms, seed, n_batches, stream):
+    """Forced detection against the analog build: throughput, and the
+    figure of merit 1 / (relative variance x time) of the projection of the
+    phantom's activity summed over 8 x 8-bin blocks, per block, FD over
+    analog.  FD: n_batches builds of one history per voxel each (batch
+    means give the variance); analog: the benchmark step's matrix, whose
+    count variance is Poisson."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = w.geometry
+    act = torch.as_tensor(w.phantom.activity.ravel().astype(np.float32)).to(dev)
+    M, N = analog.shape
+    # analog: q = A act, Var(q_j) = sum_v C_jv (act_v / n_v)^2 = (A (act^2 / n_v))_j
+    _, _, _, nv = analog.export_csc()
+    q = torch.zeros(M, dtype=torch.float32, device=dev)
+    mc.mc_project(analog, act, q)
+    qa = _blocks(q.cpu().numpy().astype(np.float64), g)
+    x2 = torch.as_tensor((w.phantom.activity.ravel().astype(np.float64) ** 2 / np.maximum(nv, 1)).astype(np.float32)).to(dev)
+    mc.mc_project(analog, x2, q)
+    va = _blocks(q.cpu().numpy().astype(np.float64), g)
+    plan = mc.Plan(w.phantom, g, "fp32", forced=True)
+    s = plan.build(0, N, seed)                      # warm-up
+    s.free()
+    qb, t_ms, t_fd, t_asm, events = [], 0.0, 0.0, 0.0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for b in range(n_batches):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s = plan.build(b * N, N, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        inf = s.info()
+        t_fd += inf["build_ms_detect"]
+        t_asm += inf["build_ms_assembly"]
+        events += inf["n_events"]
+        mc.mc_project(s, act, q)
+        qb.append(_blocks(q.cpu().numpy().astype(np.float64), g))
+        s.free()
+    plan.free()
+    qb = np.array(qb)
+    qf = qb.mean(axis=0)
+    vf = qb.var(axis=0, ddof=1) / n_batches
+    ok = (qa > 0) & (va > 0) & (vf > 0)
+    fom_a = qa[ok] ** 2 / (va[ok] * analog_ms)
+    fom_f = qf[ok] ** 2 / (vf[ok] * t_ms)
+    ratio = fom_f / fom_a
+    H = n_batches * N
+    return {"histories": H, "batches": n_batches, "histories_per_batch": N,
+            "ms": t_ms, "histories_per_s": H / (t_ms * 1e-3),
+            "fd_kernel_ms": t_fd, "assembly_ms": t_asm,
+            "weighted_events": events, "events_per_history": events / H,
+            "weighted_events_per_s": events / (t_ms * 1e-3),
+            "analog_events_per_s": analog.info()["n_events"] / (analog_ms * 1e-3),
+            "fom_block": "projection of the activity over 8x8-bin blocks",
+            "fom_ratio_median": float(np.median(ratio)),
+            "fom_ratio_p10": float(np.percentile(ratio, 10)), "fom_ratio_p90": float(np.percentile(ratio, 90)),
+            "blocks": int(ok.sum()),
+            "projection_total_rel_diff": float((qf.sum() - qa.sum()) / qa.sum()),
+            "projection_total_z": float((qf.sum() - qa.sum()) / np.sqrt(va.sum() + qb.sum(axis=1).var(ddof=1) / n_batches))}
+
+
 def run_ours(args, w):
     import torch
 
@@ -432,6 +500,10 @@ def run_ours(args, w):
     serving = None
     if args.serving_phantoms and rank == 0:
         serving = serving_benchmark(mc, int(args.serving_phantoms), int(args.serving_histories), 30, stream)
+    fd = None
+    if args.fd_batches and rank == 0:
+        analog_ms = float(np.mean(t_transport) + np.mean(t_detect) + np.mean(t_assembly))
+        fd = fd_benchmark(mc, w, last, analog_ms, seed, int(args.fd_batches), stream)
 
     # transport roofline (lane-op issue bound), work counted from an FP64
     # trace of a history sample of this workload
@@ -505,6 +577,7 @@ def run_ours(args, w):
                               "note": "benchmark matrix (largely L2-resident)"},
             "roofline_mlem_roof": roof,
             "serving": serving,
+            "forced_detection": fd,
             "mlem_value_types": value_types,
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -534,6 +607,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-phantoms", type=int, default=64, help="mixed serving batch size (0: skip)")
     ap.add_argument("--serving-histories", type=float, default=2e7, help="histories per serving phantom")
+    ap.add_argument("--fd-batches", type=int, default=8,
+                    help="forced-detection builds of one history per voxel each (0: skip)")
     ap.add_argument("--roof-histories", type=float, default=1e11,
                     help="histories of the large-matrix SpMV roofline instance (0: skip)")
     args = ap.parse_args(argv)
