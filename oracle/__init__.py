@@ -78,6 +78,7 @@ class _Problem(ctypes.Structure):
         ("window_frac", ctypes.c_double), ("photo_k", ctypes.c_double),
         ("primary_only", ctypes.c_int32),
         ("forced_detection", ctypes.c_int32),
+        ("forced_direction", ctypes.c_int32),
     ]
 
 
@@ -105,6 +106,8 @@ def lib():
                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)), ctypes.POINTER(ctypes.c_int64), vp]
             L.orc_run_w.restype = ctypes.c_int
+            L.orc_direction_band.argtypes = [P]
+            L.orc_direction_band.restype = dbl
             L.orc_kn_pdf_sr.argtypes = [dbl, dbl]
             L.orc_kn_pdf_sr.restype = dbl
             L.orc_transmission.argtypes = [P, vp, vp, dbl]
@@ -127,7 +130,10 @@ class Problem:
     """A phantom + geometry pair marshalled for the C oracle.  Keeps the
     NumPy buffers alive for as long as the struct is in use."""
 
-    def __init__(self, phantom, geometry, primary_only: bool = False, forced_detection: bool = False):
+    def __init__(self, phantom, geometry, primary_only: bool = False, forced_detection: bool = False,
+                 forced_direction: bool = False):
+        if forced_direction and not primary_only:
+            raise ValueError("forced direction is exact for unscattered photons only: use primary_only=True")
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -141,8 +147,9 @@ class Problem:
                           g.n_views, float(g.start_deg), float(g.arc_deg), g.n_bins_u, g.n_bins_v,
                           float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
                           float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
-                          int(bool(primary_only)), int(bool(forced_detection)))
+                          int(bool(primary_only)), int(bool(forced_detection)), int(bool(forced_direction)))
         self.forced_detection = bool(forced_detection)
+        self.forced_direction = bool(forced_direction)
 
     @property
     def ref(self):
@@ -215,11 +222,12 @@ def run(prob: Problem, seed: int, first: int, count: int, threads: int | None = 
 
 
 def run_fd(prob: Problem, seed: int, first: int, count: int, threads: int | None = None):
-    """Forced detection (Problem(..., forced_detection=True)): histories
-    [first, first+count).  Returns (rows int32, cols int64, q int64, fates[4]),
-    q the fixed-point weights w * 2^48 rounded to the nearest integer."""
-    if not prob.forced_detection:
-        raise ValueError("run_fd needs a Problem with forced_detection=True")
+    """Weighted transport (Problem(..., forced_detection=True) or
+    forced_direction=True): histories [first, first+count).  Returns
+    (rows int32, cols int64, q int64, fates[4]), q the fixed-point weights
+    w * 2^48 rounded to the nearest integer."""
+    if not (prob.forced_detection or prob.forced_direction):
+        raise ValueError("run_fd needs a Problem with forced_detection or forced_direction")
     if threads is None:
         threads = os.cpu_count() or 1
     L = lib()
@@ -242,6 +250,11 @@ def run_fd(prob: Problem, seed: int, first: int, count: int, threads: int | None
 
 
 FD_SCALE = 2.0 ** 48
+
+
+def direction_band(prob: Problem) -> float:
+    """Half-width in cos(theta) of the forced emission band, sin(psi_max)."""
+    return lib().orc_direction_band(prob.ref)
 
 
 def kn_pdf_sr(e_kev: float, mu: float) -> float:

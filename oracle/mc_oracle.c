@@ -52,6 +52,14 @@
  *       words); the analog photon itself is no longer detected.  Weights
  *       are tallied in fixed point, q = rint(w 2^48), so that sums are
  *       exact integers whatever their order.
+ *   R8  forced direction (same section): the emission direction is drawn
+ *       only from the band |d_z| < sin(psi_max), psi_max = atan(d/L), the
+ *       directions from which some view's collimator can be reached
+ *       (cos(theta) uniform in the band, same draws), and every detection
+ *       carries the band's share of the sphere, w = sin(psi_max).  Exact
+ *       for photons that reach the camera unscattered; scattered photons
+ *       from emissions outside the band are not simulated, so it is offered
+ *       with the primary-only tally only.
  *
  * Precision: every floating-point value is an IEEE double.  Build with
  * -ffp-contract=off so that no multiply-add is fused and the results are the
@@ -95,6 +103,7 @@ typedef struct {
   double e0_kev, window_frac, photo_k;
   int32_t primary_only; /* 1: tally only photons that never scattered */
   int32_t forced_detection; /* 1: R7 forced detection instead of analog detection */
+  int32_t forced_direction; /* 1: R8 forced emission direction (with primary_only) */
 } orc_problem;
 
 typedef struct {
@@ -455,6 +464,13 @@ static void fd_point(const orc_problem *pb, uint64_t seed, uint64_t h, uint32_t 
   }
 }
 
+/* R8: half-width of the forced emission band in cos(theta) (= its share of
+ * the sphere): sin(psi_max), tan(psi_max) = d/L. */
+double orc_direction_band(const orc_problem *pb) {
+  double tan_max = pb->hole_diam_mm / pb->hole_len_mm;
+  return tan_max / sqrt(1.0 + tan_max * tan_max);
+}
+
 /* Follow history h to its end.  Fills rec (if not NULL) and calls emit. */
 static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double mu_maj, orc_record *rec,
                         orc_emit_fn emit, orc_emit_w_fn emit_w, void *ctx) {
@@ -470,6 +486,7 @@ static void run_history(const orc_problem *pb, uint64_t seed, uint64_t h, double
   p[1] = ((double)vj + draw(&s)) * hv - 0.5 * pb->ny * hv;
   p[2] = ((double)vk + draw(&s)) * hv - 0.5 * pb->nz * hv;
   double ct = 2.0 * draw(&s) - 1.0;
+  if (pb->forced_direction) ct = ct * orc_direction_band(pb);
   double phi = 2.0 * ORC_PI * draw(&s);
   double st = sqrt(fmax(0.0, 1.0 - ct * ct));
   double d[3] = {st * cos(phi), st * sin(phi), ct};
@@ -542,9 +559,10 @@ int orc_trace(const orc_problem *pb, uint64_t seed, uint64_t first, uint64_t cou
 typedef struct {
   int32_t *row;
   int64_t *col;
-  int64_t *q; /* forced detection: fixed-point weights */
+  int64_t *q; /* fixed-point weights (1 for analog events) */
   int64_t n, cap;
   int64_t current_col;
+  int64_t q_analog; /* weight of an analog detection: 1, or R8's rint(w 2^48) */
   int failed;
 } ev_buf;
 
@@ -570,7 +588,7 @@ static void emit_to_buf_w(void *ctx, int32_t row, int64_t q) {
   b->n += 1;
 }
 
-static void emit_to_buf(void *ctx, int32_t row) { emit_to_buf_w(ctx, row, 1); }
+static void emit_to_buf(void *ctx, int32_t row) { emit_to_buf_w(ctx, row, ((ev_buf *)ctx)->q_analog); }
 
 typedef struct {
   const orc_problem *pb;
@@ -583,6 +601,7 @@ typedef struct {
 static void *worker(void *arg) {
   worker_arg *w = (worker_arg *)arg;
   int64_t n_vox = (int64_t)w->pb->nx * w->pb->ny * w->pb->nz;
+  w->buf.q_analog = w->pb->forced_direction ? (int64_t)llrint(orc_direction_band(w->pb) * ORC_FD_SCALE) : 1;
   for (uint64_t i = 0; i < w->count; ++i) {
     uint64_t h = w->first + i;
     orc_record rec;

@@ -298,3 +298,50 @@ def test_weighted_tally_sums_are_exact_integers():
     np.add.at(dense, (rows, cols), q)
     assert np.array_equal(w.toarray() * oracle.FD_SCALE, dense.astype(np.float64))
     assert w.nnz == np.count_nonzero(dense)
+
+
+def test_forced_direction_in_vacuum_is_the_acceptance_integral():
+    # vacuum, isotropic emission: with the band |cos theta| < sin(psi_max)
+    # and weight sin(psi_max) per detection, the mean weight per history and
+    # view is the per-view detection probability (1/4 pi) int_cone f dOmega
+    L, dh = 20.0, 2.0
+    ph = P.vacuum_phantom(4, 2.0)
+    g = P.Geometry(n_views=6, arc_deg=360.0, n_bins_u=64, n_bins_v=64, bin_mm=2.0,
+                   radius_mm=P.front_face_radius(4, 2.0), hole_len_mm=L, hole_diam_mm=dh, fwhm_mm=1.0)
+    pr = oracle.Problem(ph, g, primary_only=True, forced_direction=True)
+    band = oracle.direction_band(pr)
+    assert band == pytest.approx(math.sin(math.atan(dh / L)), rel=1e-15)
+
+    def integrand(th):
+        x = (L / dh) * math.tan(th)
+        return 2 * math.pi * (2 / math.pi) * (math.acos(x) - x * math.sqrt(1 - x * x)) * math.sin(th)
+
+    want = integrate.quad(integrand, 0, math.atan(dh / L), epsabs=0, epsrel=1e-12)[0] / (4 * math.pi)
+    H = 200_000
+    rows, cols, q, fates = oracle.run_fd(pr, 4, 0, H, threads=4)
+    assert np.all(q == round(band * oracle.FD_SCALE))
+    per_view = np.bincount(rows // (64 * 64), minlength=6)
+    # counts per view are binomial with p = want / band; weights w = band
+    p = want / band
+    assert np.all(np.abs(per_view - p * H) < 4.5 * math.sqrt(H * p * (1 - p)))
+    with pytest.raises(ValueError):
+        oracle.Problem(ph, g, forced_direction=True)
+
+
+def test_forced_direction_primary_agrees_with_analog_primary():
+    _, _, pa = _small_problem(False, True)
+    ph, g, _ = _small_problem(False, True)
+    pf = oracle.Problem(ph, g, primary_only=True, forced_direction=True)
+    N = N_SMALL
+    H_a = 1024 * N
+    ra, _, _ = oracle.run(pa, 21, 0, H_a)
+    blk = []
+    for b in range(16):
+        rf, _, q, _ = oracle.run_fd(pf, 41, b * 16 * N, 16 * N)
+        blk.append(_blocks(rf, q / oracle.FD_SCALE) / (16 * N))
+    blk = np.array(blk)
+    ab = _blocks(ra, None)
+    z = _z(blk, ab, ab, H_a)
+    assert np.max(np.abs(z)) < 5.0 and np.mean(z * z) < 1.6
+    # more detections per history: the band holds sin(psi_max) of the sphere
+    assert len(rf) / (16 * N) > 5 * len(ra) / H_a
