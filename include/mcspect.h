@@ -71,6 +71,16 @@ extern "C" {
  * weight sums, float values only); builds are limited to < 2^32 weighted
  * events (about 2.4e7 histories at 120 views). */
 #define MC_TALLY_FORCED 2
+/* Flag, with MC_TALLY_PRIMARY only: forced direction (same section of the
+ * paper).  The emission direction is drawn from the band |d_z| < sin(psi),
+ * tan(psi) = hole_diam/hole_len -- the directions from which some view's
+ * collimator can be reached -- with cos(theta) uniform in the band (the
+ * same draws, scaled), and every detection carries the band's share of the
+ * sphere, w = sin(psi).  Exact for unscattered photons (an unscattered
+ * photon outside the band is never detected); scattered photons from
+ * emissions outside the band would be missed, hence primary-only.  The
+ * result is a weighted system. */
+#define MC_TALLY_FORCED_DIRECTION 4
 
 /* storage type of matrix values used by the projectors */
 #define MC_VAL_F32 0

@@ -125,8 +125,15 @@ static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
     return MC_EINVAL;
   }
   if (g->precision != MC_FP32 && g->precision != MC_FP64) { set_error("precision must be MC_FP32 or MC_FP64"); return MC_EINVAL; }
-  if (g->tally < 0 || g->tally > (MC_TALLY_PRIMARY | MC_TALLY_FORCED)) {
-    set_error("tally must be MC_TALLY_ALL or MC_TALLY_PRIMARY, optionally with MC_TALLY_FORCED");
+  if (g->tally < 0 || g->tally > (MC_TALLY_PRIMARY | MC_TALLY_FORCED | MC_TALLY_FORCED_DIRECTION)) {
+    set_error("tally must be MC_TALLY_ALL or MC_TALLY_PRIMARY, optionally with MC_TALLY_FORCED or "
+              "MC_TALLY_FORCED_DIRECTION");
+    return MC_EINVAL;
+  }
+  if ((g->tally & MC_TALLY_FORCED_DIRECTION) &&
+      (!(g->tally & MC_TALLY_PRIMARY) || (g->tally & MC_TALLY_FORCED))) {
+    set_error("MC_TALLY_FORCED_DIRECTION goes with MC_TALLY_PRIMARY only (it is exact for unscattered photons; "
+              "forced detection's emission copies do not depend on the direction)");
     return MC_EINVAL;
   }
   if (ph) {
@@ -169,6 +176,7 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
   ts.precision = g->precision;
   ts.primary_only = (g->tally & MC_TALLY_PRIMARY) ? 1 : 0;
   ts.forced = (g->tally & MC_TALLY_FORCED) ? 1 : 0;
+  ts.forced_dir = (g->tally & MC_TALLY_FORCED_DIRECTION) ? 1 : 0;
   ts.weights = nullptr;
   const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
   MCS_TRY(pl.material.alloc(nv, s));
@@ -278,16 +286,19 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   // locations (one emission + the real collisions, ~2-3 per history), and
   // each location gives at most one weighted event per view.
   const bool forced = ts.forced != 0;
+  const bool weighted = forced || ts.forced_dir != 0;
+  const double band = (ts.hole_diam / ts.hole_len) / std::sqrt(1.0 + (ts.hole_diam / ts.hole_len) * (ts.hole_diam / ts.hole_len));
   const uint64_t kChunk = forced ? (1ull << 20) : (1ull << 27);
   const uint64_t n_chunks = (count + kChunk - 1) / kChunk;
   const uint64_t chunk_max = count < kChunk ? count : kChunk;
   const double tan_max = ts.hole_diam / ts.hole_len;
   const double acc = tan_max * tan_max / 16.0;
   double est = forced ? (double)count * (double)ts.n_views * 2.0 + 65536.0
-                      : (double)count * (double)ts.n_views * acc * 1.25 + 65536.0;
+                      : (double)count * (double)ts.n_views * acc * 1.25 / (ts.forced_dir ? band : 1.0) + 65536.0;
   if (est > 4.0e9) est = 4.0e9;
   const double w_max = tan_max / std::sqrt(1.0 + tan_max * tan_max) * 1.02 + 1e-6;
-  double est_q = forced ? (double)chunk_max * 3.0 + 65536.0 : (double)chunk_max * w_max * 1.1 + 65536.0;
+  double est_q = forced ? (double)chunk_max * 3.0 + 65536.0
+                        : (double)chunk_max * (ts.forced_dir ? 1.0 : w_max * 1.1) + 65536.0;
   if (!forced && est_q > (double)chunk_max) est_q = (double)chunk_max;
   unsigned long long cap = (unsigned long long)est, cap_q = (unsigned long long)est_q;
   DevBuf events, ctr, esc, weights;
@@ -304,7 +315,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   const size_t qb = forced ? fd_rec_bytes(ts.precision) : escape_rec_bytes(ts.precision);
   for (int attempt = 0; attempt < 3; ++attempt) {
     if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
-    if (forced && (rc = weights.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
+    if (weighted && (rc = weights.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
     if ((rc = esc.alloc(cap_q * qb, s))) return fail(rc);
     if (cudaMemsetAsync(ctr.p, 0, kCounters * sizeof(unsigned long long), s) != cudaSuccess) {
       set_error("cudaMemsetAsync failed");
@@ -318,7 +329,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     ts.esc_capacity = cap_q;
     ts.esc_cursor = ctr.as<unsigned long long>() + 5;
     ts.records = nullptr;
-    ts.weights = forced ? weights.as<unsigned long long>() : nullptr;
+    ts.weights = weighted ? weights.as<unsigned long long>() : nullptr;
     for (uint64_t c = 0; c < n_chunks; ++c) {
       ts.first = first + c * kChunk;
       ts.count = (c + 1 < n_chunks) ? kChunk : count - c * kChunk;
@@ -362,7 +373,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   esc.release();
   sys->n_events = (int64_t)hctr[0];
   for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
-  rc = assemble_system(sys, events, sys->n_events, s, forced ? weights.as<uint64_t>() : nullptr);
+  rc = assemble_system(sys, events, sys->n_events, s, weighted ? weights.as<uint64_t>() : nullptr);
   if (rc) return fail(rc);
   weights.release();
   if ((rc = finish_system(sys, s))) return fail(rc);

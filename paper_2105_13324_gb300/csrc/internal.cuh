@@ -168,6 +168,7 @@ struct TransportSetup {
   int precision;
   int primary_only;            // tally only unscattered photons
   int forced;                  // forced detection: weighted copies instead of analog detection
+  int forced_dir;              // forced emission direction (primary tally): weighted analog detections
   unsigned long long *weights; // forced detection: fixed-point weight of each event (else null)
 };
 

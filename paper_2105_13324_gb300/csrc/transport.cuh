@@ -74,6 +74,9 @@ template <typename T> struct TArgs {
   unsigned long long *weights;      // forced detection: fixed-point event weights
   T cos_max, omega, omega_4pi;      // acceptance cone: cos of its half-angle, solid angle, / 4 pi
   T one_m_cos_max;                  // 1 - cos_max (float path: sin^2 from 1 - cos without cancellation)
+  int forced_dir;                   // forced emission direction: cos(theta) in (-band, band)
+  T band;                           // sin of the acceptance half-angle
+  unsigned long long q_dir;         // fixed-point weight of a detection under forced direction
 };
 
 // An escaping photon that may pass a collimator: its history, the position
@@ -353,6 +356,8 @@ struct EventSink {
   unsigned long long *events, *cursor;
   unsigned long long capacity;
   mc_history_record *rec;  // trace mode: the history's record
+  unsigned long long *weights;  // weighted tallies (forced direction): one weight per event
+  unsigned long long q;         // ... the weight of every detection
 };
 
 __device__ __forceinline__ void push_event(const EventSink &s, unsigned long long key) {
@@ -361,7 +366,10 @@ __device__ __forceinline__ void push_event(const EventSink &s, unsigned long lon
   if (g.thread_rank() == 0) base = atomicAdd(s.cursor, (unsigned long long)g.size());
   base = g.shfl(base, 0);
   const unsigned long long idx = base + g.thread_rank();
-  if (idx < s.capacity) s.events[idx] = key;
+  if (idx < s.capacity) {
+    s.events[idx] = key;
+    if (s.weights) s.weights[idx] = s.q;
+  }
 }
 
 // Offer view k to an escaping photon at p (inside the grid) moving along d.
@@ -573,7 +581,8 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       if (vj >= ny) { vj -= ny; vk += 1; }
       vk += sk;
       if (vk >= nz) vk -= nz;
-      const T ct = (T)2 * uniform<T>(rg.next()) - (T)1;
+      T ct = (T)2 * uniform<T>(rg.next()) - (T)1;
+      if (a.forced_dir) ct = ct * a.band;  // only the band a collimator can see
       T cph, sph;
       cos_sin_2pi<T>(uniform<T>(rg.next()), cph, sph);
       const T sth = sqrt0<T>((T)1 - ct * ct);
@@ -699,7 +708,7 @@ __global__ void __launch_bounds__(256) detect_kernel(const __grid_constant__ TAr
     st.n_draws = r.n_draws;
     const uint32_t v = (uint32_t)(r.h % a.n_vox);
     mc_history_record *rec = TRACE ? a.records + (r.h - a.first) : nullptr;
-    EventSink sink{a.events, a.cursor, a.capacity, rec};
+    EventSink sink{a.events, a.cursor, a.capacity, rec, a.forced_dir ? a.weights : nullptr, a.q_dir};
     detect<T, TRACE>(a, st, r.p[0], r.p[1], r.p[2], r.d[0], r.d[1], r.d[2], v, sink);
     if (TRACE) rec->n_draws = st.n_draws;
   }
@@ -1060,6 +1069,10 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.omega = (T)omega;
   a.omega_4pi = (T)(omega / (4.0 * kPi));
   a.one_m_cos_max = (T)(1.0 - cos_max);
+  const double band = tan_max / std::sqrt(1.0 + tan_max * tan_max);
+  a.forced_dir = ts.forced_dir;
+  a.band = (T)band;
+  a.q_dir = (unsigned long long)std::llrint(band * kFdScale);
 }
 
 template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStream_t s) {

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EFORMAT = 0, -1, -2, -3, -4, -5
 MC_FP32, MC_FP64 = 0, 1
 MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
-MC_TALLY_ALL, MC_TALLY_PRIMARY, MC_TALLY_FORCED = 0, 1, 2
+MC_TALLY_ALL, MC_TALLY_PRIMARY, MC_TALLY_FORCED, MC_TALLY_FORCED_DIRECTION = 0, 1, 2, 4
 FD_SCALE = 2.0 ** 48  # forced-detection weights are tallied as rint(w * 2^48)
 FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 
@@ -169,7 +169,7 @@ class _Inputs:
     """C structs for a Phantom + Geometry, keeping NumPy buffers alive."""
 
     def __init__(self, phantom: _ph.Phantom, geometry: _ph.Geometry, precision: int, primary_only: bool = False,
-                 forced: bool = False):
+                 forced: bool = False, forced_direction: bool = False):
         self.material = np.ascontiguousarray(phantom.material, dtype=np.uint8)
         self.rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
         self.zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
@@ -182,7 +182,8 @@ class _Inputs:
                               float(g.bin_mm), float(g.radius_mm), float(g.hole_len_mm), float(g.hole_diam_mm),
                               float(g.fwhm_mm), float(g.e0_kev), float(g.window_frac), float(g.photo_k),
                               int(precision),
-                              (MC_TALLY_PRIMARY if primary_only else 0) | (MC_TALLY_FORCED if forced else 0))
+                              (MC_TALLY_PRIMARY if primary_only else 0) | (MC_TALLY_FORCED if forced else 0)
+                              | (MC_TALLY_FORCED_DIRECTION if forced_direction else 0))
 
 
 def _precision(p):
@@ -269,8 +270,9 @@ class System:
 class Plan:
     """Owner of an mc_plan handle: phantom + geometry resident on the device."""
 
-    def __init__(self, phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False):
-        inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
+    def __init__(self, phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False,
+                 forced_direction=False):
+        inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced, forced_direction)
         h = ctypes.c_void_p()
         _check(load().mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), _stream_ptr(stream),
                                      ctypes.byref(h)))
@@ -293,8 +295,9 @@ class Plan:
             pass
 
 
-def mc_plan_create(phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False) -> Plan:
-    return Plan(phantom, geometry, precision, stream, primary_only, forced)
+def mc_plan_create(phantom, geometry, precision="fp32", stream=None, primary_only=False, forced=False,
+                   forced_direction=False) -> Plan:
+    return Plan(phantom, geometry, precision, stream, primary_only, forced, forced_direction)
 
 
 def mc_plan_build(plan: Plan, first: int, count: int, seed: int, stream=None) -> System:
@@ -314,8 +317,8 @@ def mc_kernel_launches() -> int:
 
 
 def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="fp32", stream=None,
-                    primary_only=False, forced=False) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
+                    primary_only=False, forced=False, forced_direction=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced, forced_direction)
     h = ctypes.c_void_p()
     _check(load().mc_build_system(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(n_histories), int(seed),
                                   _stream_ptr(stream), ctypes.byref(h)))
@@ -323,8 +326,8 @@ def mc_build_system(phantom, geometry, n_histories: int, seed: int, precision="f
 
 
 def mc_build_system_range(phantom, geometry, first: int, count: int, seed: int, precision="fp32",
-                          stream=None, primary_only=False, forced=False) -> System:
-    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced)
+                          stream=None, primary_only=False, forced=False, forced_direction=False) -> System:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, forced, forced_direction)
     h = ctypes.c_void_p()
     _check(load().mc_build_system_range(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(first), int(count),
                                         int(seed), _stream_ptr(stream), ctypes.byref(h)))
@@ -522,8 +525,8 @@ def mc_batch_free(batch: Batch):
 
 
 def mc_trace_histories(phantom, geometry, seed: int, first: int, count: int, precision="fp64",
-                       primary_only=False) -> np.ndarray:
-    inp = _Inputs(phantom, geometry, _precision(precision), primary_only)
+                       primary_only=False, forced_direction=False) -> np.ndarray:
+    inp = _Inputs(phantom, geometry, _precision(precision), primary_only, False, forced_direction)
     out = np.zeros(count, RECORD_DTYPE)
     _check(load().mc_trace_histories(ctypes.byref(inp.ph), ctypes.byref(inp.geo), int(seed), int(first),
                                      int(count), out.ctypes.data))

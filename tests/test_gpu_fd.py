@@ -167,3 +167,40 @@ def test_forced_system_drives_mlem_and_is_reproducible(mc):
         s1.set_value_type("f16", allow_rounding=True)
     with pytest.raises(mc.McError):
         mc.mc_system_subset(s1, 256, 2, 0)
+
+
+def test_forced_direction_primary_matches_oracle(mc):
+    # FP64: the same histories and draws as the oracle, so the same
+    # detections; every event weighs rint(sin(psi) 2^48): exact sums
+    ph, g = _small()
+    first, count = 500, 40 * 16 ** 3
+    pr = oracle.Problem(ph, g, primary_only=True, forced_direction=True)
+    rows, cols, q, fates = oracle.run_fd(pr, 13, first, count)
+    want = oracle.system_weights(rows, cols, q, pr.n_rows, pr.n_voxels)
+    s = mc.mc_build_system_range(ph, g, first, count, 13, precision="fp64", primary_only=True, forced_direction=True)
+    inf = s.info()
+    assert inf["weighted"] and inf["fates"] == [int(f) for f in fates]
+    cp, ri, cnt, nv = s.export_csc()
+    vals, _ = s.export_values()
+    np.testing.assert_array_equal(cp, want.indptr)
+    np.testing.assert_array_equal(ri, want.indices)
+    np.testing.assert_array_equal(vals, want.data)
+    band = oracle.direction_band(pr)
+    np.testing.assert_array_equal(vals, cnt * (round(band * mc.FD_SCALE) / mc.FD_SCALE))
+    # per-history traces agree too (same draws, same fates)
+    rec_g = mc.mc_trace_histories(ph, g, 13, first, 4000, primary_only=True, forced_direction=True)
+    rec_o = oracle.trace(pr, 13, first, 4000)
+    for f in ("fate", "n_events", "n_virtual", "n_real", "n_compton", "n_draws"):
+        np.testing.assert_array_equal(rec_g[f], rec_o[f])
+    # FP32: the same detections up to rounding
+    s32 = mc.mc_build_system_range(ph, g, first, count, 13, precision="fp32", primary_only=True,
+                                   forced_direction=True)
+    rp, _, c32 = s32.export_csr()
+    rows_g = np.bincount(np.repeat(np.arange(pr.n_rows), np.diff(rp)), weights=c32.astype(np.float64),
+                         minlength=pr.n_rows)
+    rows_o = np.bincount(rows, minlength=pr.n_rows).astype(np.float64)
+    assert np.all(np.abs(rows_g - rows_o) <= 3 * np.sqrt(rows_g + rows_o) + 1e-9)
+    assert abs(rows_g.sum() - rows_o.sum()) <= 0.01 * rows_o.sum()
+    # forced direction goes with the primary tally only
+    with pytest.raises(mc.McError):
+        mc.mc_build_system(ph, g, 100, 1, forced_direction=True)
