@@ -726,6 +726,50 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
                                           const T *c0, const T *c1, const T *c2, const float *sig_tab) {
   Energy<T> en;
   en.set(e, a, sig_tab);
+  if constexpr (!is_dbl<T>()) {
+    // float path: the same traversal without branches in the step (every
+    // lane of a warp runs the same instructions whichever axis it steps)
+    // and with reciprocal multiplies instead of divisions
+    int ix = voxel_index<float>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
+    int iy = voxel_index<float>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
+    int iz = voxel_index<float>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
+    const int sx = dx > 0.0f ? 1 : (dx < 0.0f ? -1 : 0);
+    const int sy = dy > 0.0f ? 1 : (dy < 0.0f ? -1 : 0);
+    const int sz = dz > 0.0f ? 1 : (dz < 0.0f ? -1 : 0);
+    const float rx = sx ? 1.0f / dx : 0.0f, ry = sy ? 1.0f / dy : 0.0f, rz = sz ? 1.0f / dz : 0.0f;
+    // the next face on an axis lies at (i + (s > 0)) h - half; t = (face - p) / d
+    const float ox = -a.hx - px, oy = -a.hy - py, oz = -a.hz - pz;
+    float tx = sx ? fmaf((float)(ix + (sx > 0)), a.h, ox) * rx : INFINITY;
+    float ty = sy ? fmaf((float)(iy + (sy > 0)), a.h, oy) * ry : INFINITY;
+    float tz = sz ? fmaf((float)(iz + (sz > 0)), a.h, oz) * rz : INFINITY;
+    const int nx = a.nx, nxy = a.nx * a.ny;
+    int lin = (iz * a.ny + iy) * nx + ix;
+    float t = 0.0f, sum = 0.0f;
+    const int max_steps = a.nx + a.ny + a.nz + 3;
+    for (int it = 0; it < max_steps; ++it) {
+      const int m = __ldg(a.mat + lin);
+      const bool a1 = ty < tx;
+      const float t01 = a1 ? ty : tx;
+      const bool a2 = tz < t01;              // ties go to the lower axis
+      const float t1 = a2 ? tz : t01;
+      sum = fmaf(mu_total<float>(c0, c1, c2, m, en), fmaxf(t1 - t, 0.0f), sum);
+      t = fmaxf(t, t1);
+      const bool bx = !a1 && !a2, by = a1 && !a2;
+      ix += bx ? sx : 0;
+      iy += by ? sy : 0;
+      iz += a2 ? sz : 0;
+      lin += bx ? sx : (by ? sy * nx : sz * nxy);
+      if ((unsigned)ix >= (unsigned)a.nx || (unsigned)iy >= (unsigned)a.ny || (unsigned)iz >= (unsigned)a.nz) break;
+      const int i = bx ? ix : (by ? iy : iz);
+      const int sa = bx ? sx : (by ? sy : sz);
+      const float o = bx ? ox : (by ? oy : oz), r = bx ? rx : (by ? ry : rz);
+      const float tn = fmaf((float)(i + (sa > 0)), a.h, o) * r;
+      tx = bx ? tn : tx;
+      ty = by ? tn : ty;
+      tz = a2 ? tn : tz;
+    }
+    return __expf(-sum);
+  }
   int ix = voxel_index<T>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
   int iy = voxel_index<T>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
   int iz = voxel_index<T>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
