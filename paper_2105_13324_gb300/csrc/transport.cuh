@@ -39,7 +39,7 @@ constexpr double kMec2 = 510.99895;       // electron rest energy, keV
 constexpr double kRe = 2.8179403262e-13;  // classical electron radius, cm
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSigTab = 256;              // float path: sigma_KN table over [E_low, E0]
-constexpr int kWaitCollide = 16;          // lanes waiting at a real collision before a warp handles them
+constexpr int kWaitCollide = 12;          // lanes waiting at a real collision before a warp handles them
 constexpr int kWaitEmit = 8;             // lanes waiting for a new history before a warp emits
 
 template <typename T> struct TArgs {
@@ -528,13 +528,14 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
     const bool do_emit = m_emit != 0u && (__popc(m_emit) >= a.t_emit || m_fly == 0u);
     {
       // the one Philox point: words for everything this lane does below
-      // (emission 5 + flight 2; collision: photo 1 + three rejection trials
-      // 6 + azimuth 1 + flight 2; flight 2); a scatter needing more trials
-      // draws the rest inline
+      // (emission 5 + flight 2; collision: photo 1 + four rejection trials
+      // 8 + azimuth 1 + flight 2; flight 2; the ring's 16 words hold any
+      // top-up of a lane below 12); a scatter needing more trials draws the
+      // rest inline
       uint32_t need = 0u;
       if (st == S_FLY) need = 2u;
       else if (st == S_EMIT && do_emit) need = 7u;
-      else if (st == S_COLLIDE && do_coll) need = 10u;
+      else if (st == S_COLLIDE && do_coll) need = 12u;
       while (rg.avail < need) rg.refill(a);
     }
     int fate = -1;
