@@ -16,8 +16,8 @@
 //
 // One thread follows one history at a time; when its history ends it starts
 // the next one of its grid-stride sequence (lane refill), so the warps stay
-// full until the last histories of the launch.  Each loop iteration is one
-// Woodcock flight.
+// full until the last histories of the launch.  Each loop iteration is up to
+// two Woodcock flights (the second after a virtual collision).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -529,11 +529,11 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
     {
       // the one Philox point: words for everything this lane does below
       // (emission 5 + flight 2; collision: photo 1 + four rejection trials
-      // 8 + azimuth 1 + flight 2; flight 2; the ring's 16 words hold any
-      // top-up of a lane below 12); a scatter needing more trials draws the
-      // rest inline
+      // 8 + azimuth 1 + flight 2; two flights 4; the ring's 16 words hold
+      // any top-up of a lane below 12); a scatter needing more trials, or a
+      // second flight after an emission or a collision, draws the rest inline
       uint32_t need = 0u;
-      if (st == S_FLY) need = 2u;
+      if (st == S_FLY) need = 4u;
       else if (st == S_EMIT && do_emit) need = 7u;
       else if (st == S_COLLIDE && do_coll) need = 12u;
       while (rg.avail < need) rg.refill(a);
@@ -596,8 +596,10 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       if (FD) push_fd<T>(a, a.first + cur_i, 0u, px, py, pz, dx, dy, dz, en.e, (T)1);
       if (!(a.mu_maj > (T)0)) fate = MC_FATE_ESCAPE;
     }
-    if (st == S_FLY && fate < 0) {
-      // one Woodcock flight over the majorant
+    // up to two Woodcock flights over the majorant: a lane whose first
+    // flight ends in a virtual collision flies again in the same iteration
+#pragma unroll 1
+    for (int fl = 0; fl < 2 && st == S_FLY && fate < 0; ++fl) {
       if (steps >= kStepCap) {
         fate = MC_FATE_CAP;
       } else {
