@@ -311,3 +311,32 @@ def test_reduced_precision_values_exact_counts(mc, torso_small, vt, tol):
         xs.append(x.cpu().numpy())
     sysm.set_value_type("f32")
     assert _rel_l2(xs[1], xs[0]) < tol
+
+
+def test_half_and_float_values_give_identical_images():
+    # short rows (streaming tiles): counts <= 2048 are exact in half, the
+    # products are formed in float either way and every segment is summed in
+    # the same order, so images, log-likelihoods and back-projections must be
+    # identical bit for bit
+    import torch
+    from paper_2105_13324_gb300 import build as B
+    from paper_2105_13324_gb300 import mcspect as mc
+    mc.load(B.build())
+    w = P.workload("torso64")
+    s = mc.mc_build_system(w.phantom, w.geometry, 30_000_000, 3)
+    inf = s.info()
+    assert inf["spmv_fwd"] == 0 and inf["spmv_bwd"] == 0 and inf["max_count"] <= 2048
+    q = torch.zeros(s.shape[0], device="cuda")
+    mc.mc_project(s, torch.as_tensor(w.phantom.activity.ravel()).cuda(), q)
+    y = torch.as_tensor(P.poisson_counts(q.cpu().numpy(), 1e6, 5)).cuda()
+    out = {}
+    for vt in ("f32", "f16"):
+        s.set_value_type(vt)
+        x = torch.zeros(s.shape[1], device="cuda")
+        mc.mc_mlem_init(s, y, x)
+        ll = mc.mlem_iterate(s, y, x, 7, loglik=True)
+        b = torch.zeros(s.shape[1], device="cuda")
+        mc.mc_backproject(s, y, b)
+        out[vt] = (x.cpu().numpy(), np.asarray(ll), b.cpu().numpy())
+    for a, b in zip(out["f32"], out["f16"]):
+        np.testing.assert_array_equal(a, b)
