@@ -374,24 +374,30 @@ def fd_benchmark(mc, w, analog, analog_ms, seed, n_batches, stream):
     plan.free()
     qb = np.array(qb)
     qf = qb.mean(axis=0)
+    H = n_batches * N
+    out = {"histories": H, "batches": n_batches, "histories_per_batch": N,
+           "ms": t_ms, "histories_per_s": H / (t_ms * 1e-3),
+           "fd_kernel_ms": t_fd, "assembly_ms": t_asm,
+           "weighted_events": events, "events_per_history": events / H,
+           "weighted_events_per_s": events / (t_ms * 1e-3),
+           "analog_events_per_s": analog.info()["n_events"] / (analog_ms * 1e-3),
+           "projection_total_rel_diff": float((qf.sum() - qa.sum()) / qa.sum())}
+    if n_batches < 2:
+        return out                                   # no batch variance, no figure of merit
     vf = qb.var(axis=0, ddof=1) / n_batches
     ok = (qa > 0) & (va > 0) & (vf > 0)
+    if not np.any(ok):
+        return out
     fom_a = qa[ok] ** 2 / (va[ok] * analog_ms)
     fom_f = qf[ok] ** 2 / (vf[ok] * t_ms)
     ratio = fom_f / fom_a
-    H = n_batches * N
-    return {"histories": H, "batches": n_batches, "histories_per_batch": N,
-            "ms": t_ms, "histories_per_s": H / (t_ms * 1e-3),
-            "fd_kernel_ms": t_fd, "assembly_ms": t_asm,
-            "weighted_events": events, "events_per_history": events / H,
-            "weighted_events_per_s": events / (t_ms * 1e-3),
-            "analog_events_per_s": analog.info()["n_events"] / (analog_ms * 1e-3),
-            "fom_block": "projection of the activity over 8x8-bin blocks",
-            "fom_ratio_median": float(np.median(ratio)),
-            "fom_ratio_p10": float(np.percentile(ratio, 10)), "fom_ratio_p90": float(np.percentile(ratio, 90)),
-            "blocks": int(ok.sum()),
-            "projection_total_rel_diff": float((qf.sum() - qa.sum()) / qa.sum()),
-            "projection_total_z": float((qf.sum() - qa.sum()) / np.sqrt(va.sum() + qb.sum(axis=1).var(ddof=1) / n_batches))}
+    out.update({"fom_block": "projection of the activity over 8x8-bin blocks",
+                "fom_ratio_median": float(np.median(ratio)),
+                "fom_ratio_p10": float(np.percentile(ratio, 10)), "fom_ratio_p90": float(np.percentile(ratio, 90)),
+                "blocks": int(ok.sum()),
+                "projection_total_z": float((qf.sum() - qa.sum())
+                                            / np.sqrt(va.sum() + qb.sum(axis=1).var(ddof=1) / n_batches))})
+    return out
 
 
 def run_ours(args, w):
