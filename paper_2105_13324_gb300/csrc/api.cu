@@ -47,6 +47,21 @@ int device_sm_count() {
   return cache[dev];
 }
 
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<char> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+  if (done[dev]) return;
+  done[dev] = 1;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) { (void)cudaGetLastError(); return; }
+  uint64_t keep = 32ull << 30;  // 32 GiB
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) (void)cudaGetLastError();
+}
+
 int launch_transport_f32(const TransportSetup &ts, cudaStream_t s);
 int launch_transport_f64(const TransportSetup &ts, cudaStream_t s);
 int launch_debug_kn_f32(double e, uint64_t seed, uint64_t n, double *c, double *p, cudaStream_t s);

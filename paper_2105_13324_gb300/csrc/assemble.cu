@@ -117,9 +117,16 @@ int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_
 // ---------------------------------------------------------------------------
 // LSD radix sort of u64 keys (optional u32 payload), 8-bit digits
 // ---------------------------------------------------------------------------
+// Per pass: a histogram of the digit per tile of kSortTile keys, an exclusive
+// scan of the digit-major counts (global start of each (digit, tile)), and a
+// stable scatter.  The scatter first orders the tile by digit in shared
+// memory (each key's place: the digit's start within the tile, from the
+// tile's own counts, plus the keys of that digit before it in tile order),
+// then writes the tile out in that order, so that each digit's run goes to
+// consecutive addresses.
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 keys
+constexpr int kSortRounds = 12;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 3072 keys
 
 __global__ void radix_hist_kernel(const uint64_t *keys, int64_t n, int shift, uint32_t *counts, int64_t n_tiles) {
   __shared__ uint32_t s_hist[256];
@@ -135,19 +142,43 @@ __global__ void radix_hist_kernel(const uint64_t *keys, int64_t n, int shift, ui
   counts[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = s_hist[threadIdx.x];
 }
 
-// Stable scatter: key at tile position p goes to
+// exclusive scan of one value per thread over a 256-thread block
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < warp; ++w) before += s_warp[w];
+  return before + x - v;
+}
+
+// Stable scatter: the key at tile position p goes to
 //   offset[digit][tile] + (number of earlier keys of this tile with the same digit).
-__global__ void radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
-                                     int64_t n, int shift, const uint32_t *offsets, int64_t n_tiles) {
-  __shared__ uint32_t s_base[256];
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin,
+                                                                     uint64_t *kout, uint32_t *vout, int64_t n,
+                                                                     int shift, const uint32_t *counts,
+                                                                     const uint32_t *offsets, int64_t n_tiles) {
+  __shared__ uint64_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_goff[256], s_start[256], s_run[256], s_warp[kSortThreads / 32];
   __shared__ uint32_t s_wc[kSortThreads / 32][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  s_base[threadIdx.x] = offsets[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  const int64_t tile_off = (int64_t)threadIdx.x * n_tiles + blockIdx.x;
+  s_goff[threadIdx.x] = offsets[tile_off];
+  s_start[threadIdx.x] = block_exclusive_scan_256(counts[tile_off], s_warp);
+  s_run[threadIdx.x] = 0u;
 #pragma unroll
   for (int w = 0; w < kSortThreads / 32; ++w) s_wc[w][threadIdx.x] = 0u;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  // 1. order the tile by digit in shared memory (stable)
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
     const bool valid = i < n;
@@ -159,10 +190,10 @@ __global__ void radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin, u
     if (valid && rank == 0) s_wc[warp][digit] = __popc(peers);
     __syncthreads();
     if (valid) {
-      uint32_t pos = s_base[digit] + rank;
+      uint32_t pos = s_start[digit] + s_run[digit] + rank;
       for (int w = 0; w < warp; ++w) pos += s_wc[w][digit];
-      kout[pos] = key;
-      if (vout) vout[pos] = val;
+      s_keys[pos] = key;
+      s_vals[pos] = val;
     }
     __syncthreads();
     uint32_t add = 0;
@@ -171,13 +202,23 @@ __global__ void radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin, u
       add += s_wc[w][threadIdx.x];
       s_wc[w][threadIdx.x] = 0u;
     }
-    s_base[threadIdx.x] += add;
+    s_run[threadIdx.x] += add;
     __syncthreads();
+  }
+  // 2. write the tile out in digit order: each digit's keys are consecutive
+  const int64_t left = n - base;
+  const int cnt = left < kSortTile ? (int)left : kSortTile;
+  for (int p = threadIdx.x; p < cnt; p += kSortThreads) {
+    const uint64_t key = s_keys[p];
+    const uint32_t digit = (uint32_t)((key >> shift) & 255u);
+    const uint32_t pos = s_goff[digit] + ((uint32_t)p - s_start[digit]);
+    kout[pos] = key;
+    if (vout) vout[pos] = s_vals[p];
   }
 }
 
 int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bits,
-                   bool *result_in_alt, cudaStream_t s) {
+                   bool *result_in_alt, cudaStream_t s, int first_bit) {
   *result_in_alt = false;
   if (n <= 1 || bits <= 0) return MC_OK;
   if (n >= (int64_t)0xFFFFFFFFll) {
@@ -191,12 +232,13 @@ int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t 
   uint64_t *kin = keys, *kout = keys_alt;
   uint32_t *vin = vals, *vout = vals_alt;
   bool in_alt = false;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = first_bit; shift < bits; shift += 8) {
     count_launch(); radix_hist_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, n, shift, counts.as<uint32_t>(), n_tiles);
     MCS_LAUNCHED();
     MCS_TRY(exclusive_scan_u32(counts.as<uint32_t>(), offsets.as<uint32_t>(), 256 * n_tiles, s));
     count_launch(); radix_scatter_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                                     offsets.as<uint32_t>(), n_tiles);
+                                                                     counts.as<uint32_t>(), offsets.as<uint32_t>(),
+                                                                     n_tiles);
     MCS_LAUNCHED();
     uint64_t *tk = kin; kin = kout; kout = tk;
     uint32_t *tv = vin; vin = vout; vout = tv;
@@ -241,11 +283,22 @@ __global__ void split_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m,
   }
 }
 
-__global__ void transpose_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, uint64_t n_cols,
-                                      uint64_t *tkeys) {
+// (v*M + j) -> (j << b) | v, b bits holding any column index
+__global__ void transpose_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, int b, uint64_t *tkeys) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = ukeys[u];
-    tkeys[u] = (k % m) * n_cols + (k / m);
+    tkeys[u] = ((k % m) << b) | (k / m);
+  }
+}
+
+// (j << b) | v -> column v; histogram of the row j
+__global__ void split_shifted_kernel(const uint64_t *tkeys, int64_t nu, int b, uint32_t *minor_out,
+                                     uint32_t *major_hist) {
+  const uint64_t mask = (1ull << b) - 1ull;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = tkeys[u];
+    minor_out[u] = (uint32_t)(k & mask);
+    atomicAdd(&major_hist[(uint32_t)(k >> b)], 1u);
   }
 }
 
@@ -431,7 +484,8 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
       MCS_TRY(tkeys.alloc(nu * sizeof(uint64_t), s));
       MCS_TRY(tkeys_alt.alloc(nu * sizeof(uint64_t), s));
       MCS_TRY(tcnt_alt.alloc(nu * sizeof(uint32_t), s));
-      count_launch(); transpose_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, N, tkeys.as<uint64_t>());
+      const int b = bits_for(N - 1);
+      count_launch(); transpose_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, b, tkeys.as<uint64_t>());
       MCS_LAUNCHED();
       // payload: the counts, or (weighted) the CSC position of each entry
       DevBuf tperm;
@@ -442,12 +496,14 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
       }
       uint32_t *payload = weights ? tperm.as<uint32_t>() : ucnt.as<uint32_t>();
       bool talt = false;
+      // the entries are in (v, j) order: a stable sort on the j bits of
+      // (j << b) | v alone gives (j, v) order
       MCS_TRY(radix_sort_u64(tkeys.as<uint64_t>(), tkeys_alt.as<uint64_t>(), payload,
-                             tcnt_alt.as<uint32_t>(), nu, bits_for(M * N - 1), &talt, s));
+                             tcnt_alt.as<uint32_t>(), nu, b + bits_for(M - 1), &talt, s, b));
       const uint64_t *tk = talt ? tkeys_alt.as<uint64_t>() : tkeys.as<uint64_t>();
       const uint32_t *tc = talt ? tcnt_alt.as<uint32_t>() : payload;
-      count_launch(); split_keys_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, N, nullptr, sys->col_idx.as<uint32_t>(),
-                                                     hist.as<uint32_t>());
+      count_launch(); split_shifted_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, b, sys->col_idx.as<uint32_t>(),
+                                                        hist.as<uint32_t>());
       MCS_LAUNCHED();
       if (weights) {
         MCS_TRY(sys->csr_wq.alloc(nu * sizeof(uint64_t), s));

@@ -45,6 +45,12 @@ void count_launch();
   } while (0)
 
 // Device buffer owned by host code; freed on destruction (stream-ordered).
+// Once per device: let the stream-ordered allocator's default pool keep up
+// to 32 GiB of freed memory (instead of returning it to the driver
+// at every synchronisation), so that the large, short-lived buffers of a
+// build are not mapped afresh each time.  Process-local; ends with it.
+void keep_pool_memory();
+
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
@@ -63,6 +69,7 @@ struct DevBuf {
     s = stream;
     bytes = n;
     if (n == 0) return MC_OK;
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(&p, n, stream);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -205,8 +212,10 @@ int make_stream_blocks(mc_system *sys, cudaStream_t s);
 
 // Scans / sorts (assemble.cu)
 int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of keys (and payload) on bits [first_bit, bits) of
+// the keys; the result is in keys/vals or, if *result_in_alt, in the alts.
 int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t n, int bits,
-                   bool *result_in_alt, cudaStream_t s);
+                   bool *result_in_alt, cudaStream_t s, int first_bit = 0);
 
 // ---------------------------------------------------------------------------
 // device helpers
