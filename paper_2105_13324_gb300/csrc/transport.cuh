@@ -607,13 +607,26 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
         rg.ensure(2, a);
         const T s = flight<T>(uniform<T>(rg.next()), a);
         const T qx = px + s * dx, qy = py + s * dy, qz = pz + s * dz;
-        if (!(qx >= -a.hx && qx < a.hx && qy >= -a.hy && qy < a.hy && qz >= -a.hz && qz < a.hz)) {
+        // float path: the box test on the voxel indices themselves (one
+        // floor per axis, three unsigned compares); it can differ from the
+        // coordinate test only by rounding at the grid's faces
+        int ix, iy, iz;
+        bool inside;
+        if constexpr (is_dbl<T>()) {
+          inside = qx >= -a.hx && qx < a.hx && qy >= -a.hy && qy < a.hy && qz >= -a.hz && qz < a.hz;
+          ix = voxel_index<T>(qx, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
+          iy = voxel_index<T>(qy, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
+          iz = voxel_index<T>(qz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
+        } else {
+          ix = __float2int_rd(fmaf(qx, a.inv_h, a.hx_h));
+          iy = __float2int_rd(fmaf(qy, a.inv_h, a.hy_h));
+          iz = __float2int_rd(fmaf(qz, a.inv_h, a.hz_h));
+          inside = (unsigned)ix < (unsigned)a.nx && (unsigned)iy < (unsigned)a.ny && (unsigned)iz < (unsigned)a.nz;
+        }
+        if (!inside) {
           fate = MC_FATE_ESCAPE;  // leaves from the pre-flight point p
         } else {
           px = qx; py = qy; pz = qz;
-          const int ix = voxel_index<T>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
-          const int iy = voxel_index<T>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
-          const int iz = voxel_index<T>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
           const int m = __ldg(a.mat + ((size_t)iz * a.ny + iy) * a.nx + ix);
           const T mu = mu_total<T>(s_c0, s_c1, s_c2, m, en);
           if (uniform<T>(rg.next()) * a.mu_maj < mu) {
