@@ -627,7 +627,8 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
           fate = MC_FATE_ESCAPE;  // leaves from the pre-flight point p
         } else {
           px = qx; py = qy; pz = qz;
-          const int m = __ldg(a.mat + ((size_t)iz * a.ny + iy) * a.nx + ix);
+          // 32-bit index: grids hold fewer than 2^31 voxels
+          const int m = __ldg(a.mat + (uint32_t)((iz * a.ny + iy) * a.nx + ix));
           const T mu = mu_total<T>(s_c0, s_c1, s_c2, m, en);
           if (uniform<T>(rg.next()) * a.mu_maj < mu) {
             n_real += 1;
