@@ -277,7 +277,8 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
     """Mixed-size serving batch: n_phantoms torso acquisitions (48^3..128^3,
     40-120 views), each with its own system (`histories` histories) and
     Poisson projections; reconstructed together by the batched graph, and
-    one by one (autotuned kernels) for the per-phantom latency."""
+    one by one for the per-phantom latency: with mlem_iterate (autotuned
+    kernels) and as a batch of one (one graph per request)."""
     import torch
     mix = P.serving_mix(n_phantoms, seed=5)
     systems, ys = [], []
@@ -314,11 +315,27 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         lat.append(e0.elapsed_time(e1))
+    # one request at a time through a batch of one (compacted system, one
+    # CUDA graph per reconstruction)
+    lat_g = []
+    for s, y, x in zip(systems, ys, xs):
+        b1 = mc.Batch([s], [y], [x])
+        b1.mlem(n_iter, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b1.mlem(n_iter, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat_g.append(e0.elapsed_time(e1))
+        b1.free()
     sizes = sorted({int(ph.shape[0]) for ph, _, _, _ in mix})
     out = {"phantoms": n_phantoms, "grids": sizes, "histories_per_phantom": histories, "mlem_iters": n_iter,
            "build_s": build_s, "batch_ms": batch_ms, "images_per_s": n_phantoms / (batch_ms * 1e-3),
            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
            "sequential_images_per_s": n_phantoms / (sum(lat) * 1e-3),
+           "latency_graph_ms_p50": float(np.percentile(lat_g, 50)),
+           "latency_graph_ms_p99": float(np.percentile(lat_g, 99)),
+           "sequential_graph_images_per_s": n_phantoms / (sum(lat_g) * 1e-3),
            "nnz_total": int(sum(s.info()["nnz"] for s in systems))}
     batch.free()
     for s in systems:
