@@ -303,6 +303,20 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     batch_ms = float(np.median(ms))
+    # one request at a time through a batch of one (compacted system, one
+    # CUDA graph per reconstruction); before the autotuner, which may
+    # replace a system's streaming tiles by row groups
+    lat_g = []
+    for s, y, x in zip(systems, ys, xs):
+        b1 = mc.Batch([s], [y], [x])
+        b1.mlem(n_iter, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b1.mlem(n_iter, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat_g.append(e0.elapsed_time(e1))
+        b1.free()
     lat = []
     for s, y, x in zip(systems, ys, xs):
         mc.mc_system_autotune(s)
@@ -315,19 +329,6 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         lat.append(e0.elapsed_time(e1))
-    # one request at a time through a batch of one (compacted system, one
-    # CUDA graph per reconstruction)
-    lat_g = []
-    for s, y, x in zip(systems, ys, xs):
-        b1 = mc.Batch([s], [y], [x])
-        b1.mlem(n_iter, stream)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        b1.mlem(n_iter, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        lat_g.append(e0.elapsed_time(e1))
-        b1.free()
     sizes = sorted({int(ph.shape[0]) for ph, _, _, _ in mix})
     out = {"phantoms": n_phantoms, "grids": sizes, "histories_per_phantom": histories, "mlem_iters": n_iter,
            "build_s": build_s, "batch_ms": batch_ms, "images_per_s": n_phantoms / (batch_ms * 1e-3),

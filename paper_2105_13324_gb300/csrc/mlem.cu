@@ -1238,8 +1238,10 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
   for (int k = 0; k < n; ++k) {
     const mc_system *s = sys[k];
     if (!s || !y[k] || !x[k]) { set_error("batch entry %d: NULL system or vector", k); return MC_EINVAL; }
-    if (s->n_csr_blocks <= 0 || s->n_csc_blocks <= 0 || s->value_type != MC_VAL_F32 || s->row_map.p) {
-      set_error("batch entry %d: needs a full FP32 system with streaming tiles (short rows)", k);
+    // the batch builds its own tiles over the non-empty rows and columns
+    // (an error if a row or column is longer than half a tile)
+    if (s->value_type != MC_VAL_F32 || s->row_map.p) {
+      set_error("batch entry %d: needs a full (not ordered-subset) system with FP32 values", k);
       return MC_EINVAL;
     }
     longest_vec = std::max<int64_t>(longest_vec, std::max(s->n_rows, s->n_cols) + 1);

@@ -71,3 +71,26 @@ def test_autotune_keeps_results(batch_env):
     assert np.linalg.norm(after - before) / np.linalg.norm(before) < 1e-5
     ll = mc.mlem_iterate(s, y, torch.ones(s.shape[1], device="cuda"), 3, loglik=True)
     assert np.all(np.isfinite(ll))
+
+
+def test_batch_after_autotune_and_of_a_forced_detection_system(batch_env):
+    # the batch builds its own tiles: systems the autotuner moved to row
+    # groups, and weighted (forced-detection) systems, batch like any other
+    import torch
+    mc, mix, systems, ys = batch_env
+    ph, g, counts, seed = mix[1]
+    s_fd = mc.mc_build_system(ph, g, 1 << 16, seed, forced=True)
+    assert s_fd.info()["weighted"]
+    q = torch.zeros(s_fd.shape[0], device="cuda")
+    mc.mc_project(s_fd, torch.as_tensor(ph.activity.ravel()).cuda(), q)
+    y_fd = torch.as_tensor(P.poisson_counts(q.cpu().numpy(), counts, seed)).cuda()
+    s0, y0 = systems[0], ys[0]
+    mc.mc_system_autotune(s0)
+    ref = _reference(mc, [s0, s_fd], [y0, y_fd], 12)
+    xs = [torch.zeros(s.shape[1], device="cuda") for s in (s0, s_fd)]
+    b = mc.Batch([s0, s_fd], [y0, y_fd], xs)
+    b.mlem(12)
+    torch.cuda.synchronize()
+    for x, r in zip(xs, ref):
+        assert np.linalg.norm(x.cpu().numpy() - r) / np.linalg.norm(r) < 1e-6
+    b.free()
