@@ -275,8 +275,10 @@ template <typename T> __device__ __forceinline__ T uniform(uint32_t w);
 template <> __device__ __forceinline__ double uniform<double>(uint32_t w) {
   return ((double)w + 0.5) * (1.0 / 4294967296.0);
 }
+// ((w >> 8) | 1) 2^-24 = ((w >> 9) + 1/2) 2^-23, built from the bits: the
+// float 1 + (w >> 9) 2^-23, minus 1, plus 2^-24 (every step exact)
 template <> __device__ __forceinline__ float uniform<float>(uint32_t w) {
-  return (float)((w >> 8) | 1u) * (1.0f / 16777216.0f);
+  return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.0f) + 5.9604644775390625e-8f;
 }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
