@@ -204,3 +204,26 @@ def test_forced_direction_primary_matches_oracle(mc):
     # forced direction goes with the primary tally only
     with pytest.raises(mc.McError):
         mc.mc_build_system(ph, g, 100, 1, forced_direction=True)
+
+
+def test_forced_detection_in_vacuum_and_empty_cases(mc):
+    # vacuum: every copy crosses the grid unattenuated; the FP64 build equals
+    # the oracle's (no collisions: emission copies only)
+    ph = P.vacuum_phantom(8, 4.0)
+    g = P.spect_geometry(6, 360.0, 16, 4.0, 8, 4.0, hole_len_mm=20.0, hole_diam_mm=2.0, fwhm_mm=2.0)
+    pr = oracle.Problem(ph, g, forced_detection=True)
+    rows, cols, q, fates = oracle.run_fd(pr, 2, 0, 3000)
+    want = oracle.system_weights(rows, cols, q, pr.n_rows, pr.n_voxels)
+    s = mc.mc_build_system(ph, g, 3000, 2, precision="fp64", forced=True)
+    assert s.info()["fates"] == [0, 0, 3000, 0]
+    cp, ri, _, _ = s.export_csc()
+    vals, _ = s.export_values()
+    np.testing.assert_array_equal(cp, want.indptr)
+    np.testing.assert_array_equal(ri, want.indices)
+    np.testing.assert_allclose(vals, want.data, rtol=1e-12, atol=2.0 / mc.FD_SCALE)
+    # one history; a history range starting anywhere
+    s1 = mc.mc_build_system_range(ph, g, 123_456_789, 1, 2, precision="fp64", forced=True)
+    r1, c1, q1, _ = oracle.run_fd(pr, 2, 123_456_789, 1)
+    assert s1.info()["n_events"] == len(r1) == len(np.unique(r1))
+    with pytest.raises(mc.McError):
+        mc.mc_build_system(ph, g, 0, 2, forced=True)

@@ -55,7 +55,8 @@ def _compare_traces(g, o):
 # ---------------------------------------------------------------------------
 # transport
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name,first,count", [("water32", 0, 2_000_000), ("torso64", 7_777_777, 300_000)])
+@pytest.mark.parametrize("name,first,count", [("water32", 0, 2_000_000), ("torso64", 7_777_777, 300_000),
+                                              ("torso128", 987_654_321, 200_000)])
 def test_fp64_trace_matches_oracle(mc, name, first, count):
     w = P.workload(name)
     g = mc.mc_trace_histories(w.phantom, w.geometry, w.seed, first, count, precision="fp64")
@@ -117,6 +118,28 @@ def test_fp32_tallies_within_3_sigma_of_oracle(mc, name, H):
     assert np.all(np.abs(diff.data) <= lim + 1e-12)
     # shared streams: the vast majority of entries agree exactly
     assert abs(c_gpu - c_orc).sum() <= 0.01 * c_orc.sum() + 5
+
+
+def test_fp32_bench_workload_sample_within_3_sigma(mc):
+    # the benchmark's 128^3 torso, 120 views: a range of 4e6 histories from
+    # the middle of the benchmark's 1e9, through the same plan-build path
+    # and launch configuration, against the oracle on the same range
+    w = P.workload("torso128")
+    pr = oracle.Problem(w.phantom, w.geometry)
+    first, count = 500_000_000, 4_000_000
+    plan = mc.Plan(w.phantom, w.geometry, "fp32")
+    sysm = plan.build(first, count, w.seed)
+    cp, ri, cnt, nv = sysm.export_csc()
+    c_gpu = sp.csc_matrix((cnt.astype(np.float64), ri, cp), shape=(pr.n_rows, pr.n_voxels))
+    rows, cols, fates = oracle.run(pr, w.seed, first, count)
+    c_orc = oracle.system_counts(rows, cols, pr.n_rows, pr.n_voxels).astype(np.float64)
+    np.testing.assert_array_equal(nv, oracle.histories_per_voxel(pr.n_voxels, first, count))
+    info = sysm.info()
+    for f in range(3):
+        assert abs(info["fates"][f] - int(fates[f])) <= 3 * np.sqrt(info["fates"][f] + int(fates[f])) + 1
+    assert _tally_close(np.asarray(c_gpu.sum(axis=1)).ravel(), np.asarray(c_orc.sum(axis=1)).ravel())
+    assert abs(c_gpu - c_orc).sum() <= 0.01 * c_orc.sum() + 5
+    plan.free()
 
 
 def test_fp64_compton_sampler_matches_oracle(mc):
