@@ -746,7 +746,8 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
   if constexpr (!is_dbl<T>()) {
     // float path: the same traversal without branches in the step (every
     // lane of a warp runs the same instructions whichever axis it steps)
-    // and with reciprocal multiplies instead of divisions
+    // and with reciprocal multiplies instead of divisions; face distances
+    // advance by a constant step per axis
     int ix = voxel_index<float>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
     int iy = voxel_index<float>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
     int iz = voxel_index<float>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
@@ -754,11 +755,13 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
     const int sy = dy > 0.0f ? 1 : (dy < 0.0f ? -1 : 0);
     const int sz = dz > 0.0f ? 1 : (dz < 0.0f ? -1 : 0);
     const float rx = sx ? 1.0f / dx : 0.0f, ry = sy ? 1.0f / dy : 0.0f, rz = sz ? 1.0f / dz : 0.0f;
-    // the next face on an axis lies at (i + (s > 0)) h - half; t = (face - p) / d
+    // the first face on an axis lies at (i + (s > 0)) h - half, t = (face - p) / d;
+    // each later face of that axis is h / |d| further along the ray
     const float ox = -a.hx - px, oy = -a.hy - py, oz = -a.hz - pz;
     float tx = sx ? fmaf((float)(ix + (sx > 0)), a.h, ox) * rx : INFINITY;
     float ty = sy ? fmaf((float)(iy + (sy > 0)), a.h, oy) * ry : INFINITY;
     float tz = sz ? fmaf((float)(iz + (sz > 0)), a.h, oz) * rz : INFINITY;
+    const float dtx = a.h * fabsf(rx), dty = a.h * fabsf(ry), dtz = a.h * fabsf(rz);
     const int nx = a.nx, nxy = a.nx * a.ny;
     int lin = (iz * a.ny + iy) * nx + ix;
     float t = 0.0f, sum = 0.0f;
@@ -777,13 +780,9 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
       iz += a2 ? sz : 0;
       lin += bx ? sx : (by ? sy * nx : sz * nxy);
       if ((unsigned)ix >= (unsigned)a.nx || (unsigned)iy >= (unsigned)a.ny || (unsigned)iz >= (unsigned)a.nz) break;
-      const int i = bx ? ix : (by ? iy : iz);
-      const int sa = bx ? sx : (by ? sy : sz);
-      const float o = bx ? ox : (by ? oy : oz), r = bx ? rx : (by ? ry : rz);
-      const float tn = fmaf((float)(i + (sa > 0)), a.h, o) * r;
-      tx = bx ? tn : tx;
-      ty = by ? tn : ty;
-      tz = a2 ? tn : tz;
+      tx += bx ? dtx : 0.0f;
+      ty += by ? dty : 0.0f;
+      tz += a2 ? dtz : 0.0f;
     }
     return __expf(-sum);
   }
