@@ -246,3 +246,45 @@ def test_system_counts_by_brute_force():
     for r, q in zip(rows, cols):
         want[r, q] += 1
     np.testing.assert_array_equal(c, want)
+
+
+def test_unscattered_photons_keep_the_source_energy_and_scattered_ones_obey_compton():
+    # traces: an escape without scattering leaves at exactly E0 = 140.5 keV;
+    # after one scatter the energy lies in [E0 / (1 + 2 E0 / m c^2), E0)
+    w = P.workload("water32")
+    rec = oracle.trace(oracle.Problem(w.phantom, w.geometry), w.seed, 0, 200_000)
+    esc = rec["fate"] == oracle.FATE_ESCAPE
+    prim = esc & (rec["n_compton"] == 0)
+    assert prim.sum() > 10_000
+    assert np.all(rec["e_final_kev"][prim] == 140.5)
+    one = esc & (rec["n_compton"] == 1)
+    e1 = rec["e_final_kev"][one]
+    assert one.sum() > 1000
+    assert np.all(e1 < 140.5) and np.all(e1 >= 140.5 / (1 + 2 * 140.5 / MEC2) * (1 - 1e-12))
+    assert np.all(e1 >= (1 - 0.5 * w.geometry.window_frac) * 140.5)   # still in the window
+
+
+def test_emission_is_uniform_in_its_voxel_and_detected_at_its_axial_position():
+    # vacuum, 2^3 voxels of 16 mm, a narrow collimator (d/L = 0.03, crystal
+    # ~70 mm from the source: axial spread ~1 mm), 1 mm bins, almost no blur.
+    # The axial bin of a detection is then the emission height up to that
+    # spread, so relative to its voxel's centre the detections are centred
+    # (by symmetry, whatever the spread), lie within the voxel's 16 mm (plus
+    # the spread), and are flat away from the voxel's faces.
+    n, h = 2, 16.0
+    ph = P.vacuum_phantom(n, h)
+    g = P.Geometry(n_views=4, arc_deg=360.0, n_bins_u=80, n_bins_v=80, bin_mm=1.0,
+                   radius_mm=P.front_face_radius(n, h), hole_len_mm=20.0, hole_diam_mm=0.6, fwhm_mm=0.01)
+    pr = oracle.Problem(ph, g)
+    rows, cols, _ = oracle.run(pr, 3, 0, 20_000_000, threads=4)
+    iv = (rows // 80) % 80
+    z = (iv + 0.5) - 40.0                            # bin centre, mm (grid centred on 0)
+    zc = (cols // (n * n)) * h - 0.5 * n * h + 0.5 * h  # centre height of the emitting voxel
+    rel = z - zc
+    assert len(rel) > 3000
+    assert np.all(np.abs(rel) <= 0.5 * h + 2.5)
+    assert abs(rel.mean()) < 4 * (h / math.sqrt(12)) / math.sqrt(len(rel))
+    counts = np.histogram(rel, bins=12, range=(-6.0, 6.0))[0]   # central 12 mm: flat
+    exp = counts.sum() / 12
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < stats.chi2.ppf(0.9999, 11)
