@@ -46,6 +46,14 @@ OPS_PER_FLIGHT = 32.0
 OPS_PER_SCATTER = 90.0
 OPS_PER_EMISSION = 30.0
 ALU_LANES_PER_SM = 128
+# DRAM bytes (read + write) counted by ncu for the present kernels, for the
+# `traffic` fields: transport_kernel<float> on 1e8 histories of the 128^3
+# torso (2.18 MB + 49.94 MB), per history; and one ML-EM iteration's
+# forward + back-projection stream kernels on the benchmark's 1e9-history
+# matrix (82.31 + 0.13 MB and 99.61 + 2.61 MB, single-pass capture).  To be
+# taken again (or set to None) whenever those kernels change.
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (2183168 + 49937920) / 1e8
+MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
 
 
 def _peaks():
@@ -592,12 +600,19 @@ def run_ours(args, w):
             "matrix": {"rows": M, "cols": N, "nnz": inf["nnz"], "events": inf["n_events"], "fates": inf["fates"],
                        "max_count": inf["max_count"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": achieved / alu_peak, "traffic": None, "kernel": "transport_kernel<float>",
+                         "frac": achieved / alu_peak,
+                         "traffic": (TRANSPORT_DRAM_BYTES_PER_HISTORY * min(H, 1 << 27)
+                                     if w.name == "torso128" else None),
+                         "traffic_basis": "DRAM bytes of one launch (a chunk of up to 2^27 histories), "
+                                          "from an ncu capture of 1e8 torso128 histories",
+                         "kernel": "transport_kernel<float>",
                          "ops_per_history": ops,
                          "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {sm_max_mhz:.0f} MHz"},
             "roofline_mlem": {"bound": "hbm", "achieved": mlem_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm_gbs,
                               "unit": "GB/s", "frac": mlem_bytes / (it_ms * 1e-3) / 1e9 / hbm_gbs,
-                              "traffic": None, "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
+                              "traffic": (MLEM_DRAM_BYTES_PER_ITER_1E9
+                                          if w.name == "torso128" and H == 10 ** 9 else None),
+                              "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
                               "note": "benchmark matrix (largely L2-resident)"},
             "roofline_mlem_roof": roof,
             "serving": serving,
