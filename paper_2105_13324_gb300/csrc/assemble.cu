@@ -120,10 +120,13 @@ int exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_
 // Per pass: a histogram of the digit per tile of kSortTile keys, an exclusive
 // scan of the digit-major counts (global start of each (digit, tile)), and a
 // stable scatter.  The scatter first orders the tile by digit in shared
-// memory (each key's place: the digit's start within the tile, from the
-// tile's own counts, plus the keys of that digit before it in tile order),
-// then writes the tile out in that order, so that each digit's run goes to
-// consecutive addresses.
+// memory, then writes the tile out in that order, so that each digit's run
+// goes to consecutive addresses.  Within the tile, warp w holds the
+// contiguous positions [w * 32 * kSortRounds, (w + 1) * 32 * kSortRounds):
+// each warp ranks its keys among its own keys of the same digit (running
+// per-warp digit counters), and a key's place in the ordered tile is the
+// digit's start in the tile, plus the keys of that digit in earlier warps,
+// plus its rank -- the tile order, so the sort is stable.
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 12;
 constexpr int kSortTile = kSortThreads * kSortRounds;  // 3072 keys
@@ -160,60 +163,82 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 
 // Stable scatter: the key at tile position p goes to
 //   offset[digit][tile] + (number of earlier keys of this tile with the same digit).
+template <bool VALS>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t *kin, const uint32_t *vin,
                                                                      uint64_t *kout, uint32_t *vout, int64_t n,
                                                                      int shift, const uint32_t *counts,
                                                                      const uint32_t *offsets, int64_t n_tiles) {
+  constexpr int kWarps = kSortThreads / 32;
+  constexpr int kWarpKeys = 32 * kSortRounds;
+  constexpr uint32_t kNone = 0xFFFFFFFFu;
   __shared__ uint64_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_goff[256], s_start[256], s_run[256], s_warp[kSortThreads / 32];
-  __shared__ uint32_t s_wc[kSortThreads / 32][256];
+  __shared__ uint32_t s_vals[VALS ? kSortTile : 1];
+  __shared__ uint32_t s_goff[256], s_start[256], s_warp[kWarps];
+  __shared__ uint32_t s_wc[kWarps][256];  // per warp and digit: keys so far, then the warp's start in the tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile_off = (int64_t)threadIdx.x * n_tiles + blockIdx.x;
   s_goff[threadIdx.x] = offsets[tile_off];
   s_start[threadIdx.x] = block_exclusive_scan_256(counts[tile_off], s_warp);
-  s_run[threadIdx.x] = 0u;
 #pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) s_wc[w][threadIdx.x] = 0u;
+  for (int w = 0; w < kWarps; ++w) s_wc[w][threadIdx.x] = 0u;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  // 1. order the tile by digit in shared memory (stable)
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-    const bool valid = i < n;
-    const uint64_t key = valid ? kin[i] : 0ull;
-    const uint32_t val = (valid && vin) ? vin[i] : 0u;
-    const uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-    const uint32_t rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) s_wc[warp][digit] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = s_start[digit] + s_run[digit] + rank;
-      for (int w = 0; w < warp; ++w) pos += s_wc[w][digit];
-      s_keys[pos] = key;
-      s_vals[pos] = val;
-    }
-    __syncthreads();
-    uint32_t add = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      add += s_wc[w][threadIdx.x];
-      s_wc[w][threadIdx.x] = 0u;
-    }
-    s_run[threadIdx.x] += add;
-    __syncthreads();
-  }
-  // 2. write the tile out in digit order: each digit's keys are consecutive
   const int64_t left = n - base;
   const int cnt = left < kSortTile ? (int)left : kSortTile;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint32_t *wc = s_wc[warp];
+  uint64_t key[kSortRounds];
+  uint32_t val[kSortRounds];
+  uint32_t slot[kSortRounds];  // digit | (rank among the warp's keys of that digit) << 8
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int p = warp * kWarpKeys + r * 32 + lane;
+    key[r] = p < cnt ? kin[base + p] : 0ull;
+    if (VALS) val[r] = p < cnt ? vin[base + p] : 0u;
+  }
+  // 1. rank each key among the warp's keys of its digit, in tile order
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const bool valid = warp * kWarpKeys + r * 32 + lane < cnt;
+    const uint32_t digit = valid ? (uint32_t)((key[r] >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0u;
+    if (valid && lane == leader) before = wc[digit];
+    before = __shfl_sync(0xffffffffu, before, leader);
+    if (valid && lane == leader) wc[digit] = before + __popc(peers);
+    __syncwarp();
+    slot[r] = valid ? digit | ((before + __popc(peers & lt_mask)) << 8) : kNone;
+  }
+  __syncthreads();
+  // 2. per digit: each warp's start in the ordered tile
+  {
+    uint32_t run = s_start[threadIdx.x];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_wc[w][threadIdx.x];
+      s_wc[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  // 3. order the tile by digit in shared memory
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    if (slot[r] != kNone) {
+      const uint32_t pos = wc[slot[r] & 255u] + (slot[r] >> 8);
+      s_keys[pos] = key[r];
+      if (VALS) s_vals[pos] = val[r];
+    }
+  }
+  __syncthreads();
+  // 4. write the tile out in digit order: each digit's keys are consecutive
   for (int p = threadIdx.x; p < cnt; p += kSortThreads) {
-    const uint64_t key = s_keys[p];
-    const uint32_t digit = (uint32_t)((key >> shift) & 255u);
+    const uint64_t k = s_keys[p];
+    const uint32_t digit = (uint32_t)((k >> shift) & 255u);
     const uint32_t pos = s_goff[digit] + ((uint32_t)p - s_start[digit]);
-    kout[pos] = key;
-    if (vout) vout[pos] = s_vals[p];
+    kout[pos] = k;
+    if (VALS) vout[pos] = s_vals[p];
   }
 }
 
@@ -236,9 +261,15 @@ int radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t 
     count_launch(); radix_hist_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, n, shift, counts.as<uint32_t>(), n_tiles);
     MCS_LAUNCHED();
     MCS_TRY(exclusive_scan_u32(counts.as<uint32_t>(), offsets.as<uint32_t>(), 256 * n_tiles, s));
-    count_launch(); radix_scatter_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                                     counts.as<uint32_t>(), offsets.as<uint32_t>(),
-                                                                     n_tiles);
+    count_launch();
+    if (vin)
+      radix_scatter_kernel<true><<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                                           counts.as<uint32_t>(),
+                                                                           offsets.as<uint32_t>(), n_tiles);
+    else
+      radix_scatter_kernel<false><<<(unsigned)n_tiles, kSortThreads, 0, s>>>(kin, nullptr, kout, nullptr, n, shift,
+                                                                            counts.as<uint32_t>(),
+                                                                            offsets.as<uint32_t>(), n_tiles);
     MCS_LAUNCHED();
     uint64_t *tk = kin; kin = kout; kout = tk;
     uint32_t *tv = vin; vin = vout; vout = tv;
@@ -283,22 +314,47 @@ __global__ void split_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m,
   }
 }
 
-// (v*M + j) -> (j << b) | v, b bits holding any column index
-__global__ void transpose_keys_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, int b, uint64_t *tkeys) {
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = ukeys[u];
-    tkeys[u] = ((k % m) << b) | (k / m);
+// Pointer array of a sorted sequence of major indices: ptr[c] = the first
+// position whose major index is >= c, ptr[n_major] = nu.  Position u writes
+// the entries c in (major of u - 1, major of u] (the last position also
+// (major, n_major]), so every entry is written once and no histogram or scan
+// is needed.
+__device__ __forceinline__ void fill_ptr(uint32_t *ptr, int64_t u, int64_t nu, int64_t major, int64_t prev,
+                                         int64_t n_major) {
+  for (int64_t c = prev + 1; c <= major; ++c) ptr[c] = (uint32_t)u;
+  if (u == nu - 1)
+    for (int64_t c = major + 1; c <= n_major; ++c) ptr[c] = (uint32_t)nu;
+}
+
+// Sorted unique keys v*M + j -> CSC row indices j, col_ptr, and the
+// transposed keys (j << b) | v for the CSR.  The loop runs the same number of
+// times on every thread of a block (the shuffle needs whole warps).
+__global__ void csc_split_kernel(const uint64_t *ukeys, int64_t nu, uint64_t m, int b, uint32_t *row_idx,
+                                 uint32_t *col_ptr, int64_t n_cols, uint64_t *tkeys) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x; u0 < nu; u0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = u0 + threadIdx.x;
+    const bool valid = u < nu;
+    const uint64_t k = valid ? ukeys[u] : 0ull;
+    const uint64_t v = k / m, j = k - v * m;
+    uint64_t vp = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) vp = (valid && u > 0) ? ukeys[u - 1] / m : 0ull;
+    if (valid) {
+      row_idx[u] = (uint32_t)j;
+      tkeys[u] = (j << b) | v;
+      fill_ptr(col_ptr, u, nu, (int64_t)v, u == 0 ? -1 : (int64_t)vp, n_cols);
+    }
   }
 }
 
-// (j << b) | v -> column v; histogram of the row j
-__global__ void split_shifted_kernel(const uint64_t *tkeys, int64_t nu, int b, uint32_t *minor_out,
-                                     uint32_t *major_hist) {
+// Sorted keys (j << b) | v -> CSR column indices v and row_ptr.
+__global__ void csr_split_kernel(const uint64_t *tkeys, int64_t nu, int b, uint32_t *col_idx, uint32_t *row_ptr,
+                                 int64_t n_rows) {
   const uint64_t mask = (1ull << b) - 1ull;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = tkeys[u];
-    minor_out[u] = (uint32_t)(k & mask);
-    atomicAdd(&major_hist[(uint32_t)(k >> b)], 1u);
+    col_idx[u] = (uint32_t)(k & mask);
+    fill_ptr(row_ptr, u, nu, (int64_t)(k >> b), u == 0 ? -1 : (int64_t)(tkeys[u - 1] >> b), n_rows);
   }
 }
 
@@ -342,23 +398,33 @@ __global__ void iota_kernel(uint32_t *out, int64_t n) {
     out[i] = (uint32_t)i;
 }
 
+// A CSC entry's weight sum and count side by side, so that the CSR can
+// gather both with one 16-byte load.
+struct alignas(16) WEntry {
+  uint64_t w;
+  uint32_t cnt, pad;
+};
+
 __global__ void run_weights_kernel(const uint32_t *upos, const uint32_t *ucnt, int64_t nu, const uint32_t *perm,
-                                   const uint64_t *w, uint64_t *wsum) {
+                                   const uint64_t *w, uint64_t *wsum, WEntry *ent) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
     uint64_t acc = 0;
-    const uint32_t b = upos[u], e = b + ucnt[u];
+    const uint32_t c = ucnt[u], b = upos[u], e = b + c;
     for (uint32_t k = b; k < e; ++k) acc += w[perm[k]];
     wsum[u] = acc;
+    WEntry x;
+    x.w = acc; x.cnt = c; x.pad = 0u;
+    ent[u] = x;
   }
 }
 
-// out_cnt[i] = cnt[perm[i]], out_w[i] = w[perm[i]]
-__global__ void gather_entries_kernel(const uint32_t *perm, int64_t n, const uint32_t *cnt, const uint64_t *w,
-                                      uint32_t *out_cnt, uint64_t *out_w) {
+// out_cnt[i] = ent[perm[i]].cnt, out_w[i] = ent[perm[i]].w
+__global__ void gather_entries_kernel(const uint32_t *perm, int64_t n, const WEntry *ent, uint32_t *out_cnt,
+                                      uint64_t *out_w) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = perm[i];
-    out_cnt[i] = cnt[k];
-    out_w[i] = w[k];
+    const WEntry x = ent[perm[i]];
+    out_cnt[i] = x.cnt;
+    out_w[i] = x.w;
   }
 }
 
@@ -397,7 +463,7 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
 
   // 1. sort events by (v, j); weighted: with the event index as payload
   sys->weighted = weights != nullptr;
-  DevBuf alt, perm, perm_alt, wsum;
+  DevBuf alt, perm, perm_alt, went;
   MCS_TRY(alt.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint64_t), s));
   if (weights) {
     MCS_TRY(perm.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t), s));
@@ -413,7 +479,8 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
   const uint64_t *sorted = in_alt ? alt.as<uint64_t>() : keys.as<uint64_t>();
   const uint32_t *sorted_perm = weights ? (in_alt ? perm_alt.as<uint32_t>() : perm.as<uint32_t>()) : nullptr;
 
-  // 2. run-length encode
+  // 2. run-length encode; weighted: the CSC weight sums, and each entry's
+  // weight and count side by side for the CSR gather
   int64_t nu = 0;
   DevBuf ukeys, ucnt;
   if (n > 0) {
@@ -437,10 +504,11 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
     count_launch(); run_lengths_kernel<<<grid_for(nu), 256, 0, s>>>(upos.as<uint32_t>(), nu, n, ucnt.as<uint32_t>());
     MCS_LAUNCHED();
     if (weights) {
-      MCS_TRY(wsum.alloc(nu * sizeof(uint64_t), s));
+      MCS_TRY(sys->csc_wq.alloc(nu * sizeof(uint64_t), s));
+      MCS_TRY(went.alloc(nu * sizeof(WEntry), s));
       count_launch();
       run_weights_kernel<<<grid_for(nu), 256, 0, s>>>(upos.as<uint32_t>(), ucnt.as<uint32_t>(), nu, sorted_perm,
-                                                      weights, wsum.as<uint64_t>());
+                                                      weights, sys->csc_wq.as<uint64_t>(), went.as<WEntry>());
       MCS_LAUNCHED();
     }
   }
@@ -450,45 +518,38 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
   keys.release();
   sys->nnz = nu;
 
-  // 3. CSC: col_ptr from a histogram of v, rows and counts in sorted order
+  // 3. CSC: rows, counts and col_ptr in sorted order; the transposed keys
   const size_t nnz_b = (size_t)(nu > 0 ? nu : 1);
+  const int b = bits_for(N - 1);
+  DevBuf tkeys;
   {
-    DevBuf hist;
-    MCS_TRY(hist.alloc((N + 1) * sizeof(uint32_t), s));
-    MCS_CUDA(cudaMemsetAsync(hist.p, 0, (N + 1) * sizeof(uint32_t), s));
     MCS_TRY(sys->col_ptr.alloc((N + 1) * sizeof(uint32_t), s));
     MCS_TRY(sys->row_idx.alloc(nnz_b * sizeof(uint32_t), s));
     MCS_TRY(sys->csc_cnt.alloc(nnz_b * sizeof(uint32_t), s));
+    if (weights && nu == 0) MCS_TRY(sys->csc_wq.alloc(sizeof(uint64_t), s));
     if (nu > 0) {
-      count_launch(); split_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, nullptr, sys->row_idx.as<uint32_t>(),
-                                                     hist.as<uint32_t>());
+      MCS_TRY(tkeys.alloc(nu * sizeof(uint64_t), s));
+      count_launch();
+      csc_split_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, b, sys->row_idx.as<uint32_t>(),
+                                                    sys->col_ptr.as<uint32_t>(), (int64_t)N, tkeys.as<uint64_t>());
       MCS_LAUNCHED();
       MCS_CUDA(cudaMemcpyAsync(sys->csc_cnt.p, ucnt.p, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    }
-    MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), (int64_t)N + 1, s));
-    if (weights) {
-      MCS_TRY(sys->csc_wq.alloc(nnz_b * sizeof(uint64_t), s));
-      if (nu > 0) MCS_CUDA(cudaMemcpyAsync(sys->csc_wq.p, wsum.p, nu * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+      MCS_CUDA(cudaMemsetAsync(sys->col_ptr.p, 0, (N + 1) * sizeof(uint32_t), s));
     }
   }
+  ukeys.release();
 
-  // 4. CSR: sort (j*N + v, count) pairs, then row_ptr from a histogram of j
+  // 4. CSR: sort the transposed keys (with the counts, or, weighted, the CSC
+  // position of each entry), then columns and row_ptr in sorted order
   {
-    DevBuf tkeys, tkeys_alt, tcnt_alt, hist;
-    MCS_TRY(hist.alloc((M + 1) * sizeof(uint32_t), s));
-    MCS_CUDA(cudaMemsetAsync(hist.p, 0, (M + 1) * sizeof(uint32_t), s));
     MCS_TRY(sys->row_ptr.alloc((M + 1) * sizeof(uint32_t), s));
     MCS_TRY(sys->col_idx.alloc(nnz_b * sizeof(uint32_t), s));
     MCS_TRY(sys->csr_cnt.alloc(nnz_b * sizeof(uint32_t), s));
     if (nu > 0) {
-      MCS_TRY(tkeys.alloc(nu * sizeof(uint64_t), s));
+      DevBuf tkeys_alt, tcnt_alt, tperm;
       MCS_TRY(tkeys_alt.alloc(nu * sizeof(uint64_t), s));
       MCS_TRY(tcnt_alt.alloc(nu * sizeof(uint32_t), s));
-      const int b = bits_for(N - 1);
-      count_launch(); transpose_keys_kernel<<<grid_for(nu), 256, 0, s>>>(ukeys.as<uint64_t>(), nu, M, b, tkeys.as<uint64_t>());
-      MCS_LAUNCHED();
-      // payload: the counts, or (weighted) the CSC position of each entry
-      DevBuf tperm;
       if (weights) {
         MCS_TRY(tperm.alloc(nu * sizeof(uint32_t), s));
         count_launch(); iota_kernel<<<grid_for(nu), 256, 0, s>>>(tperm.as<uint32_t>(), nu);
@@ -502,23 +563,26 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
                              tcnt_alt.as<uint32_t>(), nu, b + bits_for(M - 1), &talt, s, b));
       const uint64_t *tk = talt ? tkeys_alt.as<uint64_t>() : tkeys.as<uint64_t>();
       const uint32_t *tc = talt ? tcnt_alt.as<uint32_t>() : payload;
-      count_launch(); split_shifted_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, b, sys->col_idx.as<uint32_t>(),
-                                                        hist.as<uint32_t>());
+      count_launch();
+      csr_split_kernel<<<grid_for(nu), 256, 0, s>>>(tk, nu, b, sys->col_idx.as<uint32_t>(),
+                                                    sys->row_ptr.as<uint32_t>(), (int64_t)M);
       MCS_LAUNCHED();
       if (weights) {
         MCS_TRY(sys->csr_wq.alloc(nu * sizeof(uint64_t), s));
         count_launch();
-        gather_entries_kernel<<<grid_for(nu), 256, 0, s>>>(tc, nu, ucnt.as<uint32_t>(), wsum.as<uint64_t>(),
-                                                           sys->csr_cnt.as<uint32_t>(), sys->csr_wq.as<uint64_t>());
+        gather_entries_kernel<<<grid_for(nu), 256, 0, s>>>(tc, nu, went.as<WEntry>(), sys->csr_cnt.as<uint32_t>(),
+                                                           sys->csr_wq.as<uint64_t>());
         MCS_LAUNCHED();
       } else {
         MCS_CUDA(cudaMemcpyAsync(sys->csr_cnt.p, tc, nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
       }
-    } else if (weights) {
-      MCS_TRY(sys->csr_wq.alloc(sizeof(uint64_t), s));
+    } else {
+      MCS_CUDA(cudaMemsetAsync(sys->row_ptr.p, 0, (M + 1) * sizeof(uint32_t), s));
+      if (weights) MCS_TRY(sys->csr_wq.alloc(sizeof(uint64_t), s));
     }
-    MCS_TRY(exclusive_scan_u32(hist.as<uint32_t>(), sys->row_ptr.as<uint32_t>(), (int64_t)M + 1, s));
   }
+  tkeys.release();
+  went.release();
 
   // 5. column sums S_v and the largest count
   {
