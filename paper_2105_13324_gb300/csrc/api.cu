@@ -168,10 +168,59 @@ static int check_geometry(const mc_geometry *g, const mc_phantom *ph) {
 // the attenuation coefficients, ready for any number of builds.
 struct mc_plan {
   mcs::TransportSetup ts;
-  mcs::DevBuf material, views_d, views_f, coef_d, coef_f, sig_tab;
+  mcs::DevBuf material, views_d, views_f, coef_d, coef_f, sig_tab, skip;
 };
 
 namespace mcs {
+
+// One pass of the distance map: D(v) = 1 + min over the 26 neighbours u inside
+// the grid of (material u == material v ? D(u) : 0), capped.  Starting from
+// D = 1 everywhere, pass k gives min(distance, k + 1).
+__global__ void skip_pass_kernel(const uint8_t *mat, int nx, int ny, int nz, const uint8_t *din, uint8_t *dout,
+                                 int cap) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(v % nx), iy = (int)((v / nx) % ny), iz = (int)(v / ((int64_t)nx * ny));
+    const uint8_t m = mat[v];
+    int lo = cap - 1;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int z = iz + dz;
+      if (z < 0 || z >= nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = iy + dy;
+        if (y < 0 || y >= ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = ix + dx;
+          if (x < 0 || x >= nx || (dx == 0 && dy == 0 && dz == 0)) continue;
+          const int64_t u = ((int64_t)z * ny + y) * nx + x;
+          const int du = mat[u] == m ? (int)din[u] : 0;
+          lo = du < lo ? du : lo;
+        }
+      }
+    }
+    dout[v] = (uint8_t)(lo + 1);
+  }
+}
+
+int build_skip_map(const uint8_t *material, int nx, int ny, int nz, uint8_t *skip, cudaStream_t s) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  DevBuf tmp;
+  MCS_TRY(tmp.alloc((size_t)n, s));
+  MCS_CUDA(cudaMemsetAsync(skip, 1, (size_t)n, s));
+  int64_t g = (n + 255) / 256;
+  if (g > (int64_t)device_sm_count() * 32) g = (int64_t)device_sm_count() * 32;
+  uint8_t *a = skip, *b = tmp.as<uint8_t>();
+  // kSkipCap - 1 passes (an odd count: the last pass writes into tmp, copied back)
+  for (int pass = 0; pass < kSkipCap - 1; ++pass) {
+    count_launch();
+    skip_pass_kernel<<<(int)g, 256, 0, s>>>(material, nx, ny, nz, a, b, kSkipCap);
+    MCS_LAUNCHED();
+    uint8_t *t = a; a = b; b = t;
+  }
+  if (a != skip) MCS_CUDA(cudaMemcpyAsync(skip, a, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
 
 static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t s, mc_plan &pl) {
   TransportSetup &ts = pl.ts;
@@ -226,6 +275,12 @@ static int prepare_plan(const mc_phantom *ph, const mc_geometry *g, cudaStream_t
   ts.coef_d_dev = pl.coef_d.as<double>();
   ts.coef_f_dev = pl.coef_f.as<float>();
   ts.sig_tab_dev = pl.sig_tab.as<float>();
+  ts.skip_dev = nullptr;
+  if (ts.forced && ts.precision == MC_FP32) {
+    MCS_TRY(pl.skip.alloc(nv, s));
+    MCS_TRY(build_skip_map(ts.material_dev, ts.nx, ts.ny, ts.nz, pl.skip.as<uint8_t>(), s));
+    ts.skip_dev = pl.skip.as<uint8_t>();
+  }
   return MC_OK;
 }
 

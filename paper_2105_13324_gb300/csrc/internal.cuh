@@ -159,6 +159,7 @@ struct TransportSetup {
   const double *coef_d_dev;   // [3*n_mat] 0.1 rho, N_A Z/A, k Z^4 (double)
   const float *coef_f_dev;    // [3*n_mat] 0.1 rho N_A Z/A, 0.1 rho k Z^4, 0 (float)
   const float *sig_tab_dev;   // float path: sigma_KN over the energy window
+  const uint8_t *skip_dev;    // float forced detection: distance map (see build_skip_map), else null
   // run
   uint64_t first, count;
   uint32_t key0, key1;
@@ -178,6 +179,14 @@ struct TransportSetup {
   int forced_dir;              // forced emission direction (primary tally): weighted analog detections
   unsigned long long *weights; // forced detection: fixed-point weight of each event (else null)
 };
+
+// Distance map of a material grid for the float forced-detection traversal:
+// skip[v] = the largest D <= kSkipCap such that every voxel of the grid within
+// chessboard distance D - 1 of v holds v's material (voxels outside the grid
+// do not count).  A ray inside voxel v stays in that cube of constant mu until
+// it crosses one of the cube's faces, so the traversal can cross it in one step.
+constexpr int kSkipCap = 16;
+int build_skip_map(const uint8_t *material, int nx, int ny, int nz, uint8_t *skip, cudaStream_t s);
 
 // forced detection: event weights are tallied as q = rint(w * 2^48)
 constexpr double kFdScale = 281474976710656.0;

@@ -47,6 +47,7 @@ template <typename T> struct TArgs {
   const T *coef;     // per material: double {0.1 rho, N_A Z/A, k Z^4}; float {0.1 rho N_A Z/A, 0.1 rho k Z^4}
   const T *view_cs;  // [2V] cos, sin of theta_k
   const float *sig_tab;  // [kSigTab] sigma_KN at E_low + i (E0 - E_low)/(kSigTab - 1)
+  const uint8_t *skip;   // float forced detection: distance map of the material grid
   uint32_t rk[20];   // Philox round keys: round r uses (rk[2r], rk[2r+1])
   int nx, ny, nz, n_mat;
   T h, hx, hy, hz;   // voxel size, half extents
@@ -744,10 +745,14 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
   Energy<T> en;
   en.set(e, a, sig_tab);
   if constexpr (!is_dbl<T>()) {
-    // float path: the same traversal without branches in the step (every
-    // lane of a warp runs the same instructions whichever axis it steps)
-    // and with reciprocal multiplies instead of divisions; face distances
-    // advance by a constant step per axis
+    // float path: the same integral, crossing a whole cube of constant mu per
+    // step.  The distance map gives, for the current voxel, the half-width
+    // D - 1 of the cube around it that holds one material; the ray leaves that
+    // cube at the (D - 1)-th face beyond the voxel's own next face on one
+    // axis, so mu times the length up to there is the exact integral over
+    // the cube (D = 1 is one ordinary voxel step).  Face distances advance by
+    // a constant step per axis, reciprocal multiplies replace divisions, and
+    // the step has no branches.
     int ix = voxel_index<float>(px, a.hx, a.h, a.inv_h, a.hx_h, a.nx);
     int iy = voxel_index<float>(py, a.hy, a.h, a.inv_h, a.hy_h, a.ny);
     int iz = voxel_index<float>(pz, a.hz, a.h, a.inv_h, a.hz_h, a.nz);
@@ -762,27 +767,38 @@ __device__ __forceinline__ T transmission(const TArgs<T> &a, T px, T py, T pz, T
     float ty = sy ? fmaf((float)(iy + (sy > 0)), a.h, oy) * ry : INFINITY;
     float tz = sz ? fmaf((float)(iz + (sz > 0)), a.h, oz) * rz : INFINITY;
     const float dtx = a.h * fabsf(rx), dty = a.h * fabsf(ry), dtz = a.h * fabsf(rz);
-    const int nx = a.nx, nxy = a.nx * a.ny;
-    int lin = (iz * a.ny + iy) * nx + ix;
+    const float kx_per = fabsf(dx) * a.inv_h, ky_per = fabsf(dy) * a.inv_h, kz_per = fabsf(dz) * a.inv_h;
+    // the ray leaves the grid at the last face of the first axis to run out
+    const float t_grid =
+        fminf(fminf(sx ? fmaf((float)(sx > 0 ? a.nx - 1 - ix : ix), dtx, tx) : INFINITY,
+                    sy ? fmaf((float)(sy > 0 ? a.ny - 1 - iy : iy), dty, ty) : INFINITY),
+              sz ? fmaf((float)(sz > 0 ? a.nz - 1 - iz : iz), dtz, tz) : INFINITY);
+    const int nx = a.nx, ny = a.ny;
+    int lin = (iz * ny + iy) * nx + ix;
     float t = 0.0f, sum = 0.0f;
     const int max_steps = a.nx + a.ny + a.nz + 3;
     for (int it = 0; it < max_steps; ++it) {
       const int m = __ldg(a.mat + lin);
-      const bool a1 = ty < tx;
-      const float t01 = a1 ? ty : tx;
-      const bool a2 = tz < t01;              // ties go to the lower axis
-      const float t1 = a2 ? tz : t01;
-      sum = fmaf(mu_total<float>(c0, c1, c2, m, en), fmaxf(t1 - t, 0.0f), sum);
-      t = fmaxf(t, t1);
-      const bool bx = !a1 && !a2, by = a1 && !a2;
-      ix += bx ? sx : 0;
-      iy += by ? sy : 0;
-      iz += a2 ? sz : 0;
-      lin += bx ? sx : (by ? sy * nx : sz * nxy);
+      const int D = __ldg(a.skip + lin);
+      const float e = (float)(D - 1);
+      const float cx = fmaf(e, dtx, tx), cy = fmaf(e, dty, ty), cz = fmaf(e, dtz, tz);
+      const float tc = fminf(fminf(fminf(cx, cy), cz), t_grid);
+      sum = fmaf(mu_total<float>(c0, c1, c2, m, en), fmaxf(tc - t, 0.0f), sum);
+      t = fmaxf(t, tc);
+      if (tc >= t_grid) break;
+      // faces crossed on each axis up to tc: all D on the axis that leaves
+      // the cube, floor((tc - t_axis) / step) + 1 on the others
+      const int kx = cx == tc ? D : (tx <= tc ? min((int)((tc - tx) * kx_per) + 1, D) : 0);
+      const int ky = cy == tc ? D : (ty <= tc ? min((int)((tc - ty) * ky_per) + 1, D) : 0);
+      const int kz = cz == tc ? D : (tz <= tc ? min((int)((tc - tz) * kz_per) + 1, D) : 0);
+      ix += sx * kx;
+      iy += sy * ky;
+      iz += sz * kz;
       if ((unsigned)ix >= (unsigned)a.nx || (unsigned)iy >= (unsigned)a.ny || (unsigned)iz >= (unsigned)a.nz) break;
-      tx += bx ? dtx : 0.0f;
-      ty += by ? dty : 0.0f;
-      tz += a2 ? dtz : 0.0f;
+      tx = fmaf((float)kx, dtx, tx);
+      ty = fmaf((float)ky, dty, ty);
+      tz = fmaf((float)kz, dtz, tz);
+      lin = (iz * ny + iy) * nx + ix;
     }
     return __expf(-sum);
   }
@@ -1074,6 +1090,7 @@ template <typename T> void make_targs(const TransportSetup &ts, TArgs<T> &a) {
   a.view_cs = std::is_same<T, double>::value ? (const T *)(const void *)ts.view_cs_dev
                                              : (const T *)(const void *)ts.view_cs_f_dev;
   a.sig_tab = ts.sig_tab_dev;
+  a.skip = ts.skip_dev;
   round_keys(ts.key0, ts.key1, a.rk);
   a.nx = ts.nx; a.ny = ts.ny; a.nz = ts.nz; a.n_mat = ts.n_mat;
   a.h = (T)ts.h;
@@ -1139,6 +1156,10 @@ template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStrea
   TArgs<T> a;
   make_targs<T>(ts, a);
   if (ts.count == 0) return MC_OK;
+  if (ts.forced && !is_dbl<T>() && !ts.skip_dev) {
+    set_error("float forced detection needs the plan's distance map");
+    return MC_EINVAL;
+  }
   const int threads = 256;
   int per_sm = 0;
   if (ts.forced) {

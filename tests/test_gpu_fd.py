@@ -5,7 +5,9 @@
 - FP64 transport + forced copies: the same matrix as the oracle's, entry by
   entry, on a small problem and on the full 128^3 x 120-view geometry (a
   short history range), for all photons and for the unscattered part;
-- FP32: the same events up to rounding (totals, views, entries);
+- FP32: the same events up to rounding (totals, views, entries), on the
+  small problem and on the full geometry, where the float traversal crosses
+  whole cubes of one material per step;
 - the matrix drives ML-EM like any other system, and builds are
   reproducible bit for bit (integer weight sums do not depend on the order
   in which events arrive).
@@ -139,6 +141,28 @@ def test_fp32_forced_detection_matches_oracle(mc):
     assert len(common) >= 0.999 * len(uk)
     rel = np.abs(vals[ia] - sums[ib] / mc.FD_SCALE) / (sums[ib] / mc.FD_SCALE)
     assert np.mean(rel > 1e-3) < 1e-3
+
+
+def test_fp32_forced_detection_matches_oracle_full_geometry(mc):
+    # large homogeneous regions (body, lungs, air): the float traversal's
+    # cube steps must give the same transmissions as the oracle's voxel walk
+    w = P.workload("torso128")
+    first, count = 777_777, 3000
+    pr, rows, cols, q, uk, sums, fates = _oracle_fd(w.phantom, w.geometry, 11, first, count)
+    s = mc.mc_build_system_range(w.phantom, w.geometry, first, count, 11, precision="fp32", forced=True)
+    key, vals, cnt, nv = _csc(s)
+    want = sums / mc.FD_SCALE
+    assert vals.sum() == pytest.approx(want.sum(), rel=3e-5)
+    M = pr.n_rows
+    per_view = M // w.geometry.n_views
+    view_g = np.bincount((key % M) // per_view, weights=vals, minlength=w.geometry.n_views)
+    view_o = np.bincount((uk % M) // per_view, weights=want, minlength=w.geometry.n_views)
+    np.testing.assert_allclose(view_g, view_o, rtol=2e-4)
+    common, ia, ib = np.intersect1d(key, uk, return_indices=True)
+    assert len(common) >= 0.999 * len(uk)
+    rel = np.abs(vals[ia] - want[ib]) / want[ib]
+    assert np.mean(rel > 1e-3) < 1e-3
+    assert np.median(rel) < 5e-5
 
 
 def test_forced_system_drives_mlem_and_is_reproducible(mc):
