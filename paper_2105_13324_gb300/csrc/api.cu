@@ -987,4 +987,20 @@ int mc_debug_beam(const mc_phantom *phantom, const mc_geometry *geometry, uint64
   return MC_OK;
 }
 
+int mc_debug_distance_map(const mc_phantom *phantom, uint8_t *out_host) {
+  clear_error();
+  MCS_TRY(check_phantom(phantom));
+  if (!out_host) { set_error("NULL output"); return MC_EINVAL; }
+  cudaStream_t s = nullptr;
+  const size_t nv = (size_t)phantom->nx * phantom->ny * phantom->nz;
+  DevBuf mat, map;
+  MCS_TRY(mat.alloc(nv, s));
+  MCS_TRY(map.alloc(nv, s));
+  MCS_CUDA(cudaMemcpyAsync(mat.p, phantom->material_host, nv, cudaMemcpyHostToDevice, s));
+  MCS_TRY(build_skip_map(mat.as<uint8_t>(), phantom->nx, phantom->ny, phantom->nz, map.as<uint8_t>(), s));
+  MCS_CUDA(cudaMemcpyAsync(out_host, map.p, nv, cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
 }  // extern "C"

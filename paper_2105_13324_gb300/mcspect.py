@@ -36,7 +36,8 @@ EXPORTED = (
     "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
     "mc_prior_quadratic_f64", "mc_pgd_step", "mc_system_autotune", "mc_batch_create", "mc_batch_mlem",
     "mc_batch_free",
-    "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_kernel_launches", "mc_last_error",
+    "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_debug_distance_map", "mc_kernel_launches",
+    "mc_last_error",
 )
 
 RECORD_DTYPE = np.dtype([
@@ -130,6 +131,7 @@ def load(path: str | None = None):
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
             "mc_debug_beam": [vp, vp, u64, u64, vp, vp, dbl, vp],
+            "mc_debug_distance_map": [vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -538,6 +540,20 @@ def mc_debug_kn(e_kev: float, seed: int, n: int, precision="fp64"):
     e = np.zeros(n, np.float64)
     _check(load().mc_debug_kn(float(e_kev), _precision(precision), int(seed), int(n), c.ctypes.data, e.ctypes.data))
     return c, e
+
+
+def mc_debug_distance_map(phantom) -> np.ndarray:
+    """The float forced-detection traversal's distance map, shaped like the material grid."""
+    mat = np.ascontiguousarray(phantom.material, dtype=np.uint8)
+    rho = np.ascontiguousarray(phantom.rho, dtype=np.float64)
+    zoa = np.ascontiguousarray(phantom.z_over_a, dtype=np.float64)
+    zeff = np.ascontiguousarray(phantom.z_eff, dtype=np.float64)
+    nz, ny, nx = mat.shape
+    ph = MCPhantom(nx, ny, nz, float(phantom.voxel_mm), mat.ctypes.data, len(rho), rho.ctypes.data,
+                   zoa.ctypes.data, zeff.ctypes.data)
+    out = np.zeros(mat.shape, np.uint8)
+    _check(load().mc_debug_distance_map(ctypes.byref(ph), out.ctypes.data))
+    return out
 
 
 def mc_debug_beam(phantom, geometry, seed: int, n: int, p0, d, e_kev: float, precision="fp64") -> int:

@@ -165,6 +165,42 @@ def test_fp32_forced_detection_matches_oracle_full_geometry(mc):
     assert np.median(rel) < 5e-5
 
 
+def _distance_map_by_definition(mat, cap=16):
+    # D(v) = the largest D <= cap whose cube of half-width D - 1 around v,
+    # clipped to the grid, holds only v's material
+    nz, ny, nx = mat.shape
+    out = np.zeros(mat.shape, np.int64)
+    for z, y, x in np.ndindex(mat.shape):
+        d = 1
+        while d < cap:
+            r = d  # try half-width d, i.e. D = d + 1
+            cube = mat[max(0, z - r):z + r + 1, max(0, y - r):y + r + 1, max(0, x - r):x + r + 1]
+            if not np.all(cube == mat[z, y, x]):
+                break
+            d += 1
+        out[z, y, x] = d
+    return out
+
+
+def test_distance_map_matches_its_definition(mc):
+    rng = np.random.default_rng(4)
+    ph, _ = _small()
+    cases = [ph.material]
+    # blobs of 3 materials on an odd-shaped grid, a one-material grid (the
+    # cap), a single voxel and a one-voxel-thick slab
+    z, y, x = np.meshgrid(np.arange(7), np.arange(9), np.arange(23), indexing="ij")
+    blob = ((x - 6) ** 2 + (y - 4) ** 2 + (z - 3) ** 2 < 10).astype(np.uint8)
+    blob[(x - 17) ** 2 + (y - 2) ** 2 < 5] = 2
+    cases += [blob, np.zeros((5, 6, 40), np.uint8), np.zeros((1, 1, 1), np.uint8),
+              (x[:3] == 11).astype(np.uint8)[:, :, :]]
+    cases.append(rng.integers(0, 2, (6, 5, 4)).astype(np.uint8))
+    for mat in cases:
+        q = P.Phantom(np.ascontiguousarray(mat), np.array([0.001, 1.0, 1.9]), np.array([0.5, 0.55, 0.52]),
+                      np.array([7.6, 7.4, 13.0]), 2.0)
+        got = mc.mc_debug_distance_map(q)
+        np.testing.assert_array_equal(got, _distance_map_by_definition(mat))
+
+
 def test_forced_system_drives_mlem_and_is_reproducible(mc):
     import torch
     ph, g = _small()
