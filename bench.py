@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -54,6 +55,19 @@ ALU_LANES_PER_SM = 128
 # taken again (or set to None) whenever those kernels change.
 TRANSPORT_DRAM_BYTES_PER_HISTORY = (2183168 + 49937920) / 1e8
 MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
+
+
+def _launch_histories(g) -> int:
+    """Histories per transport launch of an analog FP32 build: the library
+    runs the longest power-of-two chunk in 2^27..2^30 whose escape queue
+    (40-byte records for the fraction ~1.1 w_max of photons that can reach a
+    collimator) fits in 4 GiB."""
+    t = g.hole_diam_mm / g.hole_len_mm
+    q = min(1.1 * (t / math.sqrt(1.0 + t * t) * 1.02 + 1e-6), 1.0)
+    k = 1 << 27
+    while k < (1 << 30) and 2 * k * q * 40 <= 2 ** 32:
+        k *= 2
+    return k
 
 
 def _peaks():
@@ -601,10 +615,11 @@ def run_ours(args, w):
                        "max_count": inf["max_count"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                          "frac": achieved / alu_peak,
-                         "traffic": (TRANSPORT_DRAM_BYTES_PER_HISTORY * min(H, 1 << 27)
+                         "traffic": (TRANSPORT_DRAM_BYTES_PER_HISTORY * min(H, _launch_histories(w.geometry))
                                      if w.name == "torso128" else None),
-                         "traffic_basis": "DRAM bytes of one launch (a chunk of up to 2^27 histories), "
-                                          "from an ncu capture of 1e8 torso128 histories",
+                         "traffic_basis": "DRAM bytes of one launch (min(histories, "
+                                          f"{_launch_histories(w.geometry)}) histories), per history from an ncu "
+                                          "capture of 1e8 torso128 histories",
                          "kernel": "transport_kernel<float>",
                          "ops_per_history": ops,
                          "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {sm_max_mhz:.0f} MHz"},

@@ -206,6 +206,29 @@ def test_history_ranges_add_up(mc):
     np.testing.assert_array_equal(nf, na + nb)
 
 
+def test_build_over_several_launches_equals_its_ranges(mc):
+    # more histories than one transport launch takes (2^30 for this
+    # collimator): the launches' histories, escape queues and events must
+    # add up to the same matrix as two separate builds of the range's halves
+    w = P.workload("torso64")
+    H, m = (1 << 30) + 54_321, 600_000_001
+    full = mc.mc_build_system(w.phantom, w.geometry, H, 3, precision="fp32")
+    a = mc.mc_build_system_range(w.phantom, w.geometry, 0, m, 3, precision="fp32")
+    b = mc.mc_build_system_range(w.phantom, w.geometry, m, H - m, 3, precision="fp32")
+    M, N = full.shape
+
+    def mat(s):
+        cp, ri, cnt, nv = s.export_csc()
+        return sp.csc_matrix((cnt.astype(np.int64), ri, cp), shape=(M, N)), nv.astype(np.int64)
+
+    cf, nf = mat(full)
+    ca, na = mat(a)
+    cb, nb = mat(b)
+    assert (cf != ca + cb).nnz == 0
+    np.testing.assert_array_equal(nf, na + nb)
+    assert full.info()["fates"] == [x + y for x, y in zip(a.info()["fates"], b.info()["fates"])]
+
+
 # ---------------------------------------------------------------------------
 # assembly
 # ---------------------------------------------------------------------------
