@@ -357,7 +357,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   // headroom.  Queue capacity: an isotropic photon has |d_z| below the
   // collimator's acceptance bound with probability ~w_max.  Both are rerun
   // with the exact sizes if they overflow (transport is deterministic).
-  // Forced detection: chunks of 2^20 histories; the queue holds interaction
+  // Forced detection: chunks of 2^21 histories; the queue holds interaction
   // locations (one emission + the real collisions, ~2-3 per history), and
   // each location gives at most one weighted event per view.
   const bool forced = ts.forced != 0;
@@ -366,7 +366,7 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   const double tan_max = ts.hole_diam / ts.hole_len;
   const double w_max = tan_max / std::sqrt(1.0 + tan_max * tan_max) * 1.02 + 1e-6;
   const size_t qb = forced ? fd_rec_bytes(ts.precision) : escape_rec_bytes(ts.precision);
-  uint64_t kChunk = forced ? (1ull << 20) : (1ull << 27);
+  uint64_t kChunk = forced ? (1ull << 21) : (1ull << 27);
   if (!forced) {
     const double q_frac = ts.forced_dir ? 1.0 : (w_max * 1.1 < 1.0 ? w_max * 1.1 : 1.0);
     while (kChunk < (1ull << 30) && (double)(2 * kChunk) * q_frac * (double)qb <= 4294967296.0) kChunk *= 2;

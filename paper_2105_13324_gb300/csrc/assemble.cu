@@ -627,10 +627,12 @@ template <typename V> __global__ void convert_counts_kernel(const uint32_t *cnt,
     out[i] = from_count<V>(cnt[i]);
 }
 
-// weighted systems: the fixed-point weight sums as float
+// weighted systems: the fixed-point weight sums as float, rounded once from
+// the integer and scaled by 2^-48 exactly (the same value as a conversion
+// through double for sums below 2^53, without the slow FP64 unit)
 __global__ void convert_weights_kernel(const uint64_t *wq, int64_t n, float *out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)((double)wq[i] * (1.0 / kFdScale));
+    out[i] = __ull2float_rn(wq[i]) * (float)(1.0 / kFdScale);
 }
 
 int make_values(mc_system *sys, cudaStream_t s) {

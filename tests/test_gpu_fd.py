@@ -165,6 +165,29 @@ def test_fp32_forced_detection_matches_oracle_full_geometry(mc):
     assert np.median(rel) < 5e-5
 
 
+def test_forced_build_over_several_launches_equals_its_ranges(mc):
+    # more histories than one forced-detection launch takes (2^21): the
+    # integer weight sums of the launches add up exactly to those of two
+    # separate builds of the range's halves
+    import scipy.sparse as sp
+    ph, g = _small()
+    H, m = (1 << 21) + 3_333, 1_234_567
+
+    def mat(s):
+        cp, ri, cnt, nv = s.export_csc()
+        vals, _ = s.export_values()
+        M, N = s.shape
+        return (sp.csc_matrix((vals, ri, cp), shape=(M, N)), sp.csc_matrix((cnt.astype(np.int64), ri, cp), shape=(M, N)))
+
+    full = mc.mc_build_system(ph, g, H, 21, precision="fp32", forced=True)
+    a = mc.mc_build_system_range(ph, g, 0, m, 21, precision="fp32", forced=True)
+    b = mc.mc_build_system_range(ph, g, m, H - m, 21, precision="fp32", forced=True)
+    (wf, cf), (wa, ca), (wb, cb) = mat(full), mat(a), mat(b)
+    assert (cf != ca + cb).nnz == 0
+    assert (wf != wa + wb).nnz == 0
+    assert full.info()["fates"] == [x + y for x, y in zip(a.info()["fates"], b.info()["fates"])]
+
+
 def _distance_map_by_definition(mat, cap=16):
     # D(v) = the largest D <= cap whose cube of half-width D - 1 around v,
     # clipped to the grid, holds only v's material
