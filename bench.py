@@ -48,12 +48,13 @@ OPS_PER_SCATTER = 90.0
 OPS_PER_EMISSION = 30.0
 ALU_LANES_PER_SM = 128
 # DRAM bytes (read + write) counted by ncu for the present kernels, for the
-# `traffic` fields: transport_kernel<float> on 1e8 histories of the 128^3
-# torso (2.18 MB + 49.94 MB), per history; and one ML-EM iteration's
+# `traffic` fields: transport_kernel<float> in one launch of 1e9 histories of
+# the 128^3 torso (16.03 MB + 987.99 MB: mostly the escape queue, which a
+# launch of 1e8 histories keeps in L2), per history; and one ML-EM iteration's
 # forward + back-projection stream kernels on the benchmark's 1e9-history
 # matrix (82.31 + 0.13 MB and 99.61 + 2.61 MB, single-pass capture).  To be
 # taken again (or set to None) whenever those kernels change.
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (2183168 + 49937920) / 1e8
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (16029184 + 987994624) / 1e9
 MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
 
 
@@ -619,7 +620,7 @@ def run_ours(args, w):
                                      if w.name == "torso128" else None),
                          "traffic_basis": "DRAM bytes of one launch (min(histories, "
                                           f"{_launch_histories(w.geometry)}) histories), per history from an ncu "
-                                          "capture of 1e8 torso128 histories",
+                                          "capture of one 1e9-history torso128 launch",
                          "kernel": "transport_kernel<float>",
                          "ops_per_history": ops,
                          "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {sm_max_mhz:.0f} MHz"},

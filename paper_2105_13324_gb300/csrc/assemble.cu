@@ -173,12 +173,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
   constexpr uint32_t kNone = 0xFFFFFFFFu;
   __shared__ uint64_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[VALS ? kSortTile : 1];
-  __shared__ uint32_t s_goff[256], s_start[256], s_warp[kWarps];
+  __shared__ uint32_t s_shift[256], s_start[256], s_warp[kWarps];
   __shared__ uint32_t s_wc[kWarps][256];  // per warp and digit: keys so far, then the warp's start in the tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile_off = (int64_t)threadIdx.x * n_tiles + blockIdx.x;
-  s_goff[threadIdx.x] = offsets[tile_off];
-  s_start[threadIdx.x] = block_exclusive_scan_256(counts[tile_off], s_warp);
+  const uint32_t start = block_exclusive_scan_256(counts[tile_off], s_warp);
+  s_start[threadIdx.x] = start;
+  // output position of ordered-tile position p with this digit: p + shift
+  // (the digit's global start minus its start in the tile, modulo 2^32)
+  s_shift[threadIdx.x] = offsets[tile_off] - start;
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) s_wc[w][threadIdx.x] = 0u;
   __syncthreads();
@@ -235,8 +238,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint6
   // 4. write the tile out in digit order: each digit's keys are consecutive
   for (int p = threadIdx.x; p < cnt; p += kSortThreads) {
     const uint64_t k = s_keys[p];
-    const uint32_t digit = (uint32_t)((k >> shift) & 255u);
-    const uint32_t pos = s_goff[digit] + ((uint32_t)p - s_start[digit]);
+    const uint32_t pos = (uint32_t)p + s_shift[(uint32_t)((k >> shift) & 255u)];
     kout[pos] = k;
     if (VALS) vout[pos] = s_vals[p];
   }
