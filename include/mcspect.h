@@ -384,10 +384,11 @@ MC_API int mc_debug_beam(const mc_phantom *phantom, const mc_geometry *geometry,
                   const double *p0_host, const double *d_host, double e_kev, uint64_t *through_host);
 
 /* Verification of the float forced-detection traversal's distance map
- * (the transmission of Sec. 3's forced detection, as a line integral of mu):
- * out_host[v] (nz*ny*nx bytes, x fastest) = the largest D <= 16 such that
- * every voxel of the grid within chessboard distance D - 1 of voxel v holds
- * v's material (voxels outside the grid do not count).  Synchronises. */
+ * (the transmission of Sec. 4's forced detection, a line integral of mu):
+ * out_host[v] (nz*ny*nx bytes, x fastest, caller-owned) = the largest
+ * D <= 16 such that every voxel of the grid within chessboard distance D - 1
+ * of voxel v holds v's material (voxels outside the grid do not count).
+ * MC_EINVAL for an invalid phantom or a NULL out_host.  Synchronises. */
 MC_API int mc_debug_distance_map(const mc_phantom *phantom, uint8_t *out_host);
 
 /* Number of kernels this library has launched in this process (all
