@@ -18,6 +18,8 @@ import pytest
 import oracle
 from paper_2105_13324_gb300 import phantoms as P
 
+from tests.distance_map_ref import distance_map_by_definition
+
 pytestmark = pytest.mark.gpu
 
 
@@ -188,23 +190,6 @@ def test_forced_build_over_several_launches_equals_its_ranges(mc):
     assert full.info()["fates"] == [x + y for x, y in zip(a.info()["fates"], b.info()["fates"])]
 
 
-def _distance_map_by_definition(mat, cap=16):
-    # D(v) = the largest D <= cap whose cube of half-width D - 1 around v,
-    # clipped to the grid, holds only v's material
-    nz, ny, nx = mat.shape
-    out = np.zeros(mat.shape, np.int64)
-    for z, y, x in np.ndindex(mat.shape):
-        d = 1
-        while d < cap:
-            r = d  # try half-width d, i.e. D = d + 1
-            cube = mat[max(0, z - r):z + r + 1, max(0, y - r):y + r + 1, max(0, x - r):x + r + 1]
-            if not np.all(cube == mat[z, y, x]):
-                break
-            d += 1
-        out[z, y, x] = d
-    return out
-
-
 def test_distance_map_matches_its_definition(mc):
     rng = np.random.default_rng(4)
     ph, _ = _small()
@@ -221,7 +206,7 @@ def test_distance_map_matches_its_definition(mc):
         q = P.Phantom(np.ascontiguousarray(mat), np.array([0.001, 1.0, 1.9]), np.array([0.5, 0.55, 0.52]),
                       np.array([7.6, 7.4, 13.0]), 2.0)
         got = mc.mc_debug_distance_map(q)
-        np.testing.assert_array_equal(got, _distance_map_by_definition(mat))
+        np.testing.assert_array_equal(got, distance_map_by_definition(mat))
 
 
 def test_forced_system_drives_mlem_and_is_reproducible(mc):
