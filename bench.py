@@ -178,6 +178,10 @@ def oracle_sample(w, target_s: float = 12.0, max_histories: int = 400_000_000):
     pr = oracle.Problem(w.phantom, w.geometry)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
+    one = 200_000
+    oracle.run(pr, w.seed, 0, one, 1)
+    single = one / max(time.perf_counter() - t0, 1e-6)
+    t0 = time.perf_counter()
     cal = 2_000_000
     oracle.run(pr, w.seed, 0, cal, threads)
     rate = cal / max(time.perf_counter() - t0, 1e-6)
@@ -197,7 +201,8 @@ def oracle_sample(w, target_s: float = 12.0, max_histories: int = 400_000_000):
             "sample": f"histories 0..{hs - 1} of the {w.name} workload (FP64 C transport + tally + count matrix, "
                       f"{threads} threads), {dt:.1f} s; ML-EM float64 on that sample's matrix (nnz {c.nnz}): "
                       f"{1.0 / mlem_s:.2f} iter/s",
-            "histories": hs, "seconds": dt, "mlem_iter_per_s": 1.0 / mlem_s, "mlem_nnz": int(c.nnz)}
+            "histories": hs, "seconds": dt, "mlem_iter_per_s": 1.0 / mlem_s, "mlem_nnz": int(c.nnz),
+            "single_core_value": single, "single_core_sample": f"histories 0..{one - 1}, 1 thread"}
 
 
 def run_reference(args, w):
@@ -609,6 +614,7 @@ def run_ours(args, w):
                        "parallelism": f"{ws} independent acquisitions" if ws > 1 else "1 GPU"},
             "mlem_iter_per_s": 1e3 / it_ms,
             "transport_histories_per_s": H / (t_tr * 1e-3),
+            "build_histories_per_s": H / ((t_tr + float(np.mean(t_detect)) + float(np.mean(t_assembly))) * 1e-3),
             "step_breakdown_ms": {"transport": t_tr, "detect": float(np.mean(t_detect)),
                                   "assembly": float(np.mean(t_assembly)),
                                   "mlem": it_ms * n_iter},
