@@ -78,3 +78,36 @@ def test_invalid_arguments_are_rejected_on_the_host():
     rc = lib.mc_system_from_events(4, 4, rows.ctypes.data, cols.ctypes.data, 2, 0, 10, None, ctypes.byref(h))
     assert rc == mcspect.MC_EINVAL and b"out of range" in lib.mc_last_error()
     assert lib.mc_system_free(None) == mcspect.MC_OK
+
+
+def test_tally_material_and_debug_arguments_are_rejected_on_the_host():
+    # the checks of the tally flags, the material table and the debug hooks
+    # run before any device call
+    from paper_2105_13324_gb300 import phantoms as P
+    lib = mcspect.load(B.build())
+    w = P.workload("water32")
+    h = ctypes.c_void_p()
+    for kw, word in (({"forced": True, "forced_direction": True, "primary_only": True}, b"FORCED_DIRECTION"),
+                     ({"forced_direction": True}, b"FORCED_DIRECTION")):
+        inp = mcspect._Inputs(w.phantom, w.geometry, mcspect.MC_FP32, **kw)
+        rc = lib.mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), None, ctypes.byref(h))
+        assert rc == mcspect.MC_EINVAL and word in lib.mc_last_error() and not h.value
+    # a voxel whose material is not in the table
+    bad = P.Phantom(w.phantom.material.copy(), w.phantom.rho, w.phantom.z_over_a, w.phantom.z_eff,
+                    w.phantom.voxel_mm)
+    bad.material[3, 4, 5] = len(w.phantom.rho)
+    inp = mcspect._Inputs(bad, w.geometry, mcspect.MC_FP32)
+    rc = lib.mc_plan_create(ctypes.byref(inp.ph), ctypes.byref(inp.geo), None, ctypes.byref(h))
+    assert rc == mcspect.MC_EINVAL and b"outside the table" in lib.mc_last_error()
+    # the distance-map hook: no phantom, no output buffer
+    assert lib.mc_debug_distance_map(None, None) == mcspect.MC_EINVAL and b"phantom" in lib.mc_last_error()
+    inp = mcspect._Inputs(w.phantom, w.geometry, mcspect.MC_FP32)
+    assert lib.mc_debug_distance_map(ctypes.byref(inp.ph), None) == mcspect.MC_EINVAL
+    assert b"NULL output" in lib.mc_last_error()
+    # weighted events outside the matrix
+    rows = np.array([0, 4], np.int32)
+    cols = np.array([0, 1], np.int32)
+    wq = np.array([1, 2], np.uint64)
+    rc = lib.mc_system_from_weighted_events(4, 4, rows.ctypes.data, cols.ctypes.data, wq.ctypes.data, 2, 0, 10,
+                                            None, ctypes.byref(h))
+    assert rc == mcspect.MC_EINVAL and b"out of range" in lib.mc_last_error()
