@@ -2,7 +2,12 @@
 
 D(v) = the largest D <= cap such that every voxel of the grid within
 chessboard distance D - 1 of voxel v holds v's material; voxels outside the
-grid do not count.  Brute force over growing cubes: for test grids only.
+grid do not count.  Brute force over growing cubes (small test grids), and
+the same map from windowed minimum and maximum filters (any size): the cube
+of half-width r around v, clipped to the grid, holds one material iff the
+minimum and the maximum of the material over the (2r + 1)^3 window agree
+(with edge replication, the window's outside values repeat voxels inside
+the clipped cube).
 """
 import numpy as np
 
@@ -18,3 +23,13 @@ def distance_map_by_definition(mat, cap=16):
             d += 1
         out[z, y, x] = d
     return out
+
+
+def distance_map_by_filters(mat, cap=16):
+    from scipy import ndimage
+    d = np.ones(mat.shape, np.int64)
+    for r in range(1, cap):
+        lo = ndimage.minimum_filter(mat, size=2 * r + 1, mode="nearest")
+        hi = ndimage.maximum_filter(mat, size=2 * r + 1, mode="nearest")
+        d += (lo == hi) & (d == r)
+    return d

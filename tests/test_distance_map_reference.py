@@ -1,27 +1,16 @@
 """The distance map's test reference against an independent formulation.
 
 The GPU test of mc_debug_distance_map compares the library with
-distance_map_by_definition; here that brute force is checked against
-windowed minimum and maximum filters: the cube of half-width r around v,
-clipped to the grid, holds one material iff the minimum and the maximum of
-the material over the (2r + 1)^3 window agree (with edge replication, the
-window's outside values repeat voxels that lie inside the clipped cube).
+distance_map_by_definition (brute force over growing cubes); here that
+brute force is checked against the windowed minimum/maximum filter
+formulation and against values worked out by hand.
 """
 import numpy as np
 import pytest
 
-from tests.distance_map_ref import distance_map_by_definition
+from tests.distance_map_ref import distance_map_by_definition, distance_map_by_filters
 
-ndimage = pytest.importorskip("scipy.ndimage")
-
-
-def _by_filters(mat, cap=16):
-    d = np.ones(mat.shape, np.int64)
-    for r in range(1, cap):
-        lo = ndimage.minimum_filter(mat, size=2 * r + 1, mode="nearest")
-        hi = ndimage.maximum_filter(mat, size=2 * r + 1, mode="nearest")
-        d += (lo == hi) & (d == r)
-    return d
+pytest.importorskip("scipy.ndimage")
 
 
 @pytest.mark.parametrize("shape,p,seed", [((6, 7, 9), 0.15, 0), ((3, 20, 20), 0.02, 1), ((1, 1, 1), 0.5, 2),
@@ -30,7 +19,7 @@ def test_brute_force_equals_window_filters(shape, p, seed):
     rng = np.random.default_rng(seed)
     mat = (rng.random(shape) < p).astype(np.uint8)
     mat[rng.random(shape) < p / 2] = 2
-    np.testing.assert_array_equal(distance_map_by_definition(mat), _by_filters(mat))
+    np.testing.assert_array_equal(distance_map_by_definition(mat), distance_map_by_filters(mat))
 
 
 def test_known_values():
