@@ -385,6 +385,9 @@ double orc_transmission(const orc_problem *pb, const double p[3], const double d
       tn[a] = INFINITY;
     }
   }
+  /* a direction with no finite non-zero component never leaves the grid:
+     the line integral is undefined */
+  if (step[0] == 0 && step[1] == 0 && step[2] == 0) return NAN;
   double t = 0.0, sum = 0.0;
   for (;;) {
     int m = pb->material[((int64_t)idx[2] * pb->ny + idx[1]) * pb->nx + idx[0]];

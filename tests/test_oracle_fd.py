@@ -63,6 +63,15 @@ def test_transmission_uniform_grid_is_beer_lambert():
             assert oracle.transmission(pr, p, d, 140.5) == pytest.approx(want, rel=1e-12)
 
 
+def test_transmission_without_a_direction_is_undefined():
+    # a zero or NaN direction never leaves the grid: NaN, not an endless walk
+    ph = P.uniform_phantom(8, 5.0)
+    g = P.spect_geometry(4, 360.0, 8, 5.0, 8, 5.0)
+    pr = oracle.Problem(ph, g)
+    for d in (np.zeros(3), np.full(3, np.nan)):
+        assert math.isnan(oracle.transmission(pr, np.array([1.0, 2.0, 3.0]), d, 140.5))
+
+
 def test_transmission_through_layers_by_chord_lengths():
     # z-layers of water and bone over vacuum: the exponent is the sum over
     # layers of mu times the length of the ray inside the layer
