@@ -42,8 +42,6 @@ extern "C" {
 #define MC_EINVAL (-1)   /* bad argument (null pointer, size, range) */
 #define MC_ENOMEM (-2)   /* device or host allocation failed */
 #define MC_ECUDA (-3)    /* a CUDA call or kernel launch failed */
-#define MC_ETIMEOUT (-4) /* a bounded device wait ran out */
-#define MC_EFORMAT (-5)  /* malformed serialized matrix */
 
 /* transport precision */
 #define MC_FP32 0 /* production: float arithmetic, 23-bit uniforms */
@@ -352,7 +350,7 @@ MC_API int mc_batch_free(mc_batch *batch);
  * is owned by another allocator.  mlem_iterate may allocate its
  * log-likelihood buffer on first use; this entry point never calls
  * cudaMalloc, cudaFree or any allocating routine.  The paper has no
- * counterpart: it is a deployment variant of Eq. (MLEM).
+ * counterpart: it is a deployment variant of the ML-EM update above.
  *
  * Its work vectors live in one static device array of ~18 MiB that every GPU
  * loading the library keeps until the process exits.  Limits: n_rows and
@@ -362,7 +360,9 @@ MC_API int mc_batch_free(mc_batch *batch);
  * allocation); make that first call before any stream capture.  All calls on
  * a device share the array and leave their values in it: calls that overlap
  * on the GPU (other streams, other threads) race and must be serialised by
- * the caller.  Results equal mlem_iterate's on the same inputs. */
+ * the caller.  The current device must be the one the system was built on
+ * (MC_EINVAL otherwise: the array is per device).  Results equal
+ * mlem_iterate's on the same inputs. */
 MC_API int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter,
                                 double *loglik_host, void *stream);
 

@@ -2,7 +2,7 @@
 
 `project(x, system)` is A·x (Eq. (IMC) of Sec. 5.1) as a torch autograd
 function whose backward is the library's Aᵀ kernel (float32 or float64,
-following x).  `QuadraticPrior` is the 6-neighbour smoothness penalty
+following x).  `quadratic_prior` is the 6-neighbour smoothness penalty
 computed by the library.  `penalised_reconstruct` minimises
     Φ(x) = Σ_j (q_j − y_j ln q_j) + β/2 Σ_(v,w) (x_v − x_w)²,  q = A x,
 by EM-preconditioned projected gradient steps (`mc_pgd_step`); with β = 0
@@ -64,13 +64,6 @@ class _Prior(torch.autograd.Function):
 def quadratic_prior(x: torch.Tensor, shape, beta: float) -> torch.Tensor:
     """β/2 Σ over 6-neighbour pairs (x_v − x_w)², differentiable in x."""
     return _Prior.apply(x, tuple(shape), float(beta))
-
-
-def penalised_objective(x, system, y, shape, beta):
-    """Φ(x) = Σ_j (q_j − y_j ln q_j) + prior, bins with y_j = 0 adding q_j."""
-    q = project(x, system)
-    pos = y > 0
-    return q.sum() - (y[pos] * torch.log(q[pos])).sum() + quadratic_prior(x, shape, beta)
 
 
 def penalised_reconstruct(system, y, shape, beta: float, n_iter: int, alpha: float = 1.0, x0=None,

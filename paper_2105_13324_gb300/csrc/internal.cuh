@@ -96,6 +96,11 @@ struct DevBuf {
 }  // namespace mcs
 
 struct mc_system {
+  // the device current when the system was made: its buffers live there
+  mc_system() {
+    if (cudaGetDevice(&device) != cudaSuccess) device = -1;
+  }
+  int device = -1;
   int64_t n_rows = 0, n_cols = 0, nnz = 0, n_events = 0;
   uint64_t first = 0, count = 0;
   uint64_t fates[4] = {0, 0, 0, 0};

@@ -800,6 +800,16 @@ extern "C" int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, fl
     set_error("mlem_iterate_noalloc: %d forward blocks exceed the static limit %lld", fb, (long long)kNoAllocPartials);
     return MC_EINVAL;
   }
+  // the scratch array used is the current device's: it must be the device
+  // that holds the system's matrix and work vectors
+  int dev = -1;
+  MCS_CUDA(cudaGetDevice(&dev));
+  if (dev != sys->device) {
+    set_error("mlem_iterate_noalloc: the current device is %d but the system was built on device %d; make the "
+              "system's device current first",
+              dev, sys->device);
+    return MC_EINVAL;
+  }
   unsigned char *base = nullptr;
   MCS_TRY(noalloc_scratch(&base));
   float *r = reinterpret_cast<float *>(base + kNoAllocOffR);

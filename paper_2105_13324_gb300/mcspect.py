@@ -20,7 +20,7 @@ from . import phantoms as _ph
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
 
-MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_EFORMAT = 0, -1, -2, -3, -4, -5
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA = 0, -1, -2, -3
 MC_FP32, MC_FP64 = 0, 1
 MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
 MC_TALLY_ALL, MC_TALLY_PRIMARY, MC_TALLY_FORCED, MC_TALLY_FORCED_DIRECTION = 0, 1, 2, 4
