@@ -84,6 +84,11 @@ extern "C" {
 #define MC_VAL_F32 0
 #define MC_VAL_F16 1
 #define MC_VAL_BF16 2
+/* the conventional reduced-precision storage, kept for comparison: the
+ * entries A_jv = C_jv / n_v themselves rounded to half / bfloat16 (half
+ * loses precision below 6.1e-5, where A becomes subnormal) */
+#define MC_VAL_F16_A 3
+#define MC_VAL_BF16_A 4
 
 /* history fates */
 #define MC_FATE_ABSORBED 0
@@ -231,11 +236,27 @@ MC_API int mc_system_export_csc(const mc_system *sys, int64_t *col_ptr_host, int
 MC_API int mc_system_export_csr(const mc_system *sys, int64_t *row_ptr_host, int32_t *col_idx_host, uint32_t *counts_host,
                          void *stream);
 
-/* Storage type of the values the projectors read (MC_VAL_F32 default;
- * MC_VAL_F16 / MC_VAL_BF16 store the integer counts C_jv, exact up to 2048 /
- * 256, accumulation stays FP32).  Returns MC_EINVAL if a count is not exact
- * in the requested type unless allow_rounding is non-zero. */
+/* Storage type of the values the projectors read (the matrix of Eq. (IMC),
+ * Sec. 5.1; accumulation stays FP32 in every type).  MC_VAL_F32 (default),
+ * MC_VAL_F16 and MC_VAL_BF16 store the integer counts C_jv -- exact up to
+ * 2^24, 2048 and 256 -- and fold 1/n_v into the image; MC_EINVAL if a count
+ * is not exact in the requested type unless allow_rounding is non-zero, in
+ * which case the counts are rounded and ML-EM normalises with the rounded
+ * counts' column sums (it runs on the matrix the projectors read).
+ * MC_VAL_F16_A / MC_VAL_BF16_A store round(C_jv / n_v) and reconstruct with
+ * that rounded matrix (its own column sums as the sensitivity); they are
+ * always rounded.  Weighted systems keep MC_VAL_F32.  The FP64 projectors
+ * (mc_project_f64, mc_backproject_f64) always use the exact matrix. */
 MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t allow_rounding);
+
+/* Projector kernels of a system: fwd (forward projection, CSR) and bwd
+ * (back-projection, CSC) each 0 = streaming tiles (entries of runs of whole
+ * rows staged in shared memory, then one fixed-order sum per row), 1, 2, 4,
+ * 8, 16 or 32 = that many lanes per row (column), or -1 = keep.  Every
+ * layout gives the same sums up to FP32 rounding order.  Streaming tiles
+ * need every row (column) shorter than 2048 entries: MC_EINVAL otherwise
+ * (the system is left unchanged).  Synchronises `stream`. */
+MC_API int mc_system_set_spmv_layout(mc_system *sys, int32_t fwd, int32_t bwd, void *stream);
 
 /* Forward projection q = A x (Eq. (IMC)): x_dev[N], q_dev[M], float. */
 MC_API int mc_project(const mc_system *sys, const float *x_dev, float *q_dev, void *stream);

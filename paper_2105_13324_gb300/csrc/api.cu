@@ -720,12 +720,13 @@ int mc_system_export_csr(const mc_system *sys, int64_t *row_ptr_host, int32_t *c
 int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t allow_rounding) {
   clear_error();
   if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
-  if (value_type != MC_VAL_F32 && value_type != MC_VAL_F16 && value_type != MC_VAL_BF16) {
+  if (value_type != MC_VAL_F32 && value_type != MC_VAL_F16 && value_type != MC_VAL_BF16 &&
+      value_type != MC_VAL_F16_A && value_type != MC_VAL_BF16_A) {
     set_error("unknown value type %d", value_type);
     return MC_EINVAL;
   }
   const uint32_t exact = value_type == MC_VAL_F32 ? (1u << 24) : value_type == MC_VAL_F16 ? 2048u : 256u;
-  if (!allow_rounding && sys->max_count > exact) {
+  if (!values_are_a(value_type) && !allow_rounding && sys->max_count > exact) {
     set_error("largest count %u is not exact in the requested type (limit %u)", sys->max_count, exact);
     return MC_EINVAL;
   }
@@ -884,6 +885,12 @@ int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp
   if (!sens_dev || !bp_dev || !x_dev || n < 0) { set_error("NULL argument or negative size"); return MC_EINVAL; }
   if (!(alpha > 0.0) || !std::isfinite(alpha)) { set_error("alpha must be positive"); return MC_EINVAL; }
   return pgd_step(n, alpha, sens_dev, bp_dev, gp_dev, x_dev, API_STREAM(stream));
+}
+
+int mc_system_set_spmv_layout(mc_system *sys, int32_t fwd, int32_t bwd, void *stream) {
+  clear_error();
+  if (!sys) { set_error("system is NULL"); return MC_EINVAL; }
+  return set_spmv_layout(sys, fwd, bwd, API_STREAM(stream));
 }
 
 int mc_system_autotune(mc_system *sys, void *stream) {

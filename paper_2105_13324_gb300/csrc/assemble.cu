@@ -646,16 +646,105 @@ __global__ void convert_weights_kernel(const uint64_t *wq, int64_t n, float *out
     out[i] = __ull2float_rn(wq[i]) * (float)(1.0 / kFdScale);
 }
 
+// rounded-A values: val = round(C_jv / n_v) per entry of the CSR (column
+// index per entry) ...
+template <typename V> __device__ __forceinline__ V from_double(double a);
+template <> __device__ __forceinline__ __half from_double<__half>(double a) { return __double2half(a); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double a) {
+  return __double2bfloat16(a);
+}
+template <typename V>
+__global__ void a_values_csr_kernel(const uint32_t *cnt, const uint32_t *col, const uint32_t *n_v, int64_t n, V *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = from_double<V>((double)cnt[i] / (double)n_v[col[i]]);
+}
+// ... and per column of the CSC, with the column sums of the stored values
+// (the rounded matrix's sensitivity s~_v, summed in double in row order)
+template <typename V>
+__global__ void a_values_csc_kernel(const uint32_t *col_ptr, const uint32_t *cnt, const uint32_t *n_v, int64_t n_cols,
+                                    V *out, float *ones, double *sens, float *inv_sens) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_cols; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    const double nv = (double)n_v[v];
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) {
+      const V a = from_double<V>((double)cnt[k] / nv);
+      out[k] = a;
+      acc += (double)(float)a;
+    }
+    ones[v] = 1.0f;
+    sens[v] = acc;
+    inv_sens[v] = acc > 0.0 ? (float)(1.0 / acc) : 0.0f;
+  }
+}
+
+// counts rounded to V: the column sums of the stored (rounded) counts
+template <typename V>
+__global__ void rounded_count_sums_kernel(const uint32_t *col_ptr, const uint32_t *cnt, int64_t n_cols, double *sums,
+                                          float *inv_sums) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_cols; v += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (uint32_t k = col_ptr[v]; k < col_ptr[v + 1]; ++k) acc += (double)(float)from_count<V>(cnt[k]);
+    sums[v] = acc;
+    inv_sums[v] = acc > 0.0 ? (float)(1.0 / acc) : 0.0f;
+  }
+}
+
+template <typename V> static int make_rounded_sums(mc_system *sys, cudaStream_t s) {
+  const int64_t N = sys->n_cols;
+  const size_t nb = (size_t)(N > 0 ? N : 1);
+  MCS_TRY(sys->a_sens.alloc(nb * sizeof(double), s));
+  MCS_TRY(sys->a_inv_sens.alloc(nb * sizeof(float), s));
+  if (N > 0) {
+    count_launch();
+    rounded_count_sums_kernel<V><<<grid_for(N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
+                                                             N, sys->a_sens.as<double>(), sys->a_inv_sens.as<float>());
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+template <typename V> static int make_a_values(mc_system *sys, cudaStream_t s) {
+  const int64_t nnz = sys->nnz, N = sys->n_cols;
+  const size_t nb = (size_t)(N > 0 ? N : 1);
+  MCS_TRY(sys->a_ones.alloc(nb * sizeof(float), s));
+  MCS_TRY(sys->a_sens.alloc(nb * sizeof(double), s));
+  MCS_TRY(sys->a_inv_sens.alloc(nb * sizeof(float), s));
+  if (nnz > 0) {
+    count_launch();
+    a_values_csr_kernel<V><<<grid_for(nnz), 256, 0, s>>>(sys->csr_cnt.as<uint32_t>(), sys->col_idx.as<uint32_t>(),
+                                                         sys->n_v.as<uint32_t>(), nnz, sys->csr_val.as<V>());
+  }
+  if (N > 0) {
+    count_launch();
+    a_values_csc_kernel<V><<<grid_for(N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
+                                                       sys->n_v.as<uint32_t>(), N, sys->csc_val.as<V>(),
+                                                       sys->a_ones.as<float>(), sys->a_sens.as<double>(),
+                                                       sys->a_inv_sens.as<float>());
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
 int make_values(mc_system *sys, cudaStream_t s) {
   const int64_t nnz = sys->nnz;
-  const size_t es = sys->value_type == MC_VAL_F32 ? 4 : 2;
+  const size_t es = value_storage(sys->value_type) == 0 ? 4 : 2;
   const size_t bytes = (size_t)(nnz > 0 ? nnz : 1) * es;
   MCS_TRY(sys->csr_val.alloc(bytes, s));
   MCS_TRY(sys->csc_val.alloc(bytes, s));
+  if (sys->weighted && sys->value_type != MC_VAL_F32) { set_error("weighted systems keep float values"); return MC_EINVAL; }
+  if (sys->value_type == MC_VAL_F16_A) return make_a_values<__half>(sys, s);
+  if (sys->value_type == MC_VAL_BF16_A) return make_a_values<__nv_bfloat16>(sys, s);
+  // counts beyond the type's exact range are rounded: normalise with the
+  // rounded counts' column sums
+  sys->rounded_counts = (sys->value_type == MC_VAL_F16 && sys->max_count > 2048u) ||
+                        (sys->value_type == MC_VAL_BF16 && sys->max_count > 256u);
+  if (sys->rounded_counts) {
+    if (sys->value_type == MC_VAL_F16) MCS_TRY(make_rounded_sums<__half>(sys, s));
+    else MCS_TRY(make_rounded_sums<__nv_bfloat16>(sys, s));
+  }
   if (nnz == 0) return MC_OK;
   const int g = grid_for(nnz);
   if (sys->weighted) {
-    if (sys->value_type != MC_VAL_F32) { set_error("weighted systems keep float values"); return MC_EINVAL; }
     count_launch(); convert_weights_kernel<<<g, 256, 0, s>>>(sys->csr_wq.as<uint64_t>(), nnz, sys->csr_val.as<float>());
     count_launch(); convert_weights_kernel<<<g, 256, 0, s>>>(sys->csc_wq.as<uint64_t>(), nnz, sys->csc_val.as<float>());
   } else if (sys->value_type == MC_VAL_F32) {

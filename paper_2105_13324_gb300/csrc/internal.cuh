@@ -116,6 +116,16 @@ struct mc_system {
   mcs::DevBuf inv_n;    // f32 [N]: 1/n_v (0 if n_v = 0)
   mcs::DevBuf colsum;   // f64 [N]: S_v = sum_j C_jv
   mcs::DevBuf inv_colsum;  // f32 [N]: 1/S_v (0 if S_v = 0)
+  // Stored values that are not the exact counts: for the rounded-A value
+  // types (MC_VAL_F16_A, MC_VAL_BF16_A) the values are A itself, so the
+  // image is not prescaled (ones) and the normaliser is the stored matrix's
+  // column sum s~_v; for counts rounded to half / bfloat16 (allow_rounding)
+  // the normaliser is the column sum S~_v of the rounded counts.  Either
+  // way ML-EM runs on the matrix the projectors read.
+  bool rounded_counts = false;
+  mcs::DevBuf a_ones;        // f32 [N]: 1
+  mcs::DevBuf a_sens;        // f64 [N]: s~_v = sum_j val_jv (A types) or S~_v (rounded counts)
+  mcs::DevBuf a_inv_sens;    // f32 [N]: its reciprocal (0 if 0)
   // work vectors of the projectors / ML-EM
   mcs::DevBuf xs;       // f32 [N]: x_v / n_v
   mcs::DevBuf r;        // f32 [M]
@@ -143,6 +153,26 @@ struct mc_system {
 struct mc_batch;
 
 namespace mcs {
+
+// value types: storage (0 float, 1 half, 2 bfloat16) and whether the stored
+// values are A = C diag(1/n_v) itself rather than the counts C
+inline int value_storage(int vt) { return vt == MC_VAL_F16 || vt == MC_VAL_F16_A ? 1 : vt == MC_VAL_F32 ? 0 : 2; }
+inline bool values_are_a(int vt) { return vt == MC_VAL_F16_A || vt == MC_VAL_BF16_A; }
+// Scale applied to the image before the forward projection (1/n_v for
+// count values, 1 for A values), the back-projection's normaliser (1/S_v,
+// or 1/s~_v) and the sensitivity terms the start image sums (S_v with
+// per-voxel division by n_v, or s~_v as it is: n_v pointer NULL).
+inline const float *proj_scale(const mc_system *s) {
+  return values_are_a(s->value_type) ? s->a_ones.as<float>() : s->inv_n.as<float>();
+}
+inline const float *proj_inv_norm(const mc_system *s) {
+  return values_are_a(s->value_type) || s->rounded_counts ? s->a_inv_sens.as<float>() : s->inv_colsum.as<float>();
+}
+inline const double *proj_sens_terms(const mc_system *s, const uint32_t **n_v) {
+  if (values_are_a(s->value_type)) { *n_v = nullptr; return s->a_sens.as<double>(); }
+  *n_v = s->n_v.as<uint32_t>();
+  return s->rounded_counts ? s->a_sens.as<double>() : s->colsum.as<double>();
+}
 
 // ---------------------------------------------------------------------------
 // build pieces implemented in the .cu files
@@ -216,6 +246,7 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
 
 // Projector value arrays for sys->value_type.
 int make_values(mc_system *sys, cudaStream_t s);
+int set_spmv_layout(mc_system *sys, int fwd, int bwd, cudaStream_t s);
 
 // System of the rows of views subset, subset + n_sub, ... of a parent whose
 // rows are view-major with rpv rows per view (assemble.cu).

@@ -198,15 +198,18 @@ __global__ void sum_partials_kernel(const double *partials, int64_t n, double *o
   if (threadIdx.x == 0) *out = t;
 }
 
-// partials[b] = block b's sum of y (double) and of s_v = S_v / n_v
+// partials[b] = block b's sum of y (double) and of s_v = S_v / n_v (n_v
+// NULL: colsum holds s_v itself)
 __global__ void init_sums_kernel(const float *y, int64_t m, const double *colsum, const uint32_t *n_v, int64_t n,
                                  double *py, double *ps) {
   __shared__ double s_tmp[32];
   double ay = 0.0, as = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
     ay += (double)y[i];
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    if (n_v[v]) as += colsum[v] / (double)n_v[v];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!n_v) as += colsum[v];
+    else if (n_v[v]) as += colsum[v] / (double)n_v[v];
+  }
   const double ty = block_sum_double(ay, s_tmp);
   const double ts = block_sum_double(as, s_tmp);
   if (threadIdx.x == 0) { py[blockIdx.x] = ty; ps[blockIdx.x] = ts; }
@@ -234,7 +237,7 @@ __global__ void init_fill_kernel(const double *x0p, const double *colsum, const 
 
 __global__ void sensitivity_kernel(const double *colsum, const uint32_t *n_v, int64_t n, double *s) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    s[v] = n_v[v] ? colsum[v] / (double)n_v[v] : 0.0;
+    s[v] = !n_v ? colsum[v] : n_v[v] ? colsum[v] / (double)n_v[v] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -498,7 +501,7 @@ static void back_launch(const mc_system *sys, int g, const float *r, float *x, f
   const int blocks = div_up(n * g, kSpmvThreads);
   const V *val = sys->csc_val.as<V>();
   const uint32_t *cp = sys->col_ptr.as<uint32_t>(), *ri = sys->row_idx.as<uint32_t>();
-  const float *inv_n = sys->inv_n.as<float>(), *ics = sys->inv_colsum.as<float>();
+  const float *inv_n = proj_scale(sys), *ics = proj_inv_norm(sys);
   switch (g) {
     case 1: count_launch(); csc_back_kernel<V, 1, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
     case 2: count_launch(); csc_back_kernel<V, 2, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
@@ -529,7 +532,7 @@ static void stream_back_launch(const mc_system *sys, const float *r, float *x, f
   const unsigned nb = (unsigned)sys->n_csc_blocks;
   const uint32_t *cp = sys->col_ptr.as<uint32_t>(), *t = sys->csc_blocks.as<uint32_t>(), *ri = sys->row_idx.as<uint32_t>();
   const V *val = sys->csc_val.as<V>();
-  const float *inv_n = sys->inv_n.as<float>(), *ics = sys->inv_colsum.as<float>();
+  const float *inv_n = proj_scale(sys), *ics = proj_inv_norm(sys);
   count_launch();
   if (sys->warp_rows_bwd)
     stream_back_kernel<V, true, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
@@ -541,29 +544,29 @@ template <int MODE, bool LL>
 static void fwd_dispatch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
                          cudaStream_t s, const uint32_t *rmap = nullptr, const float *add = nullptr) {
   if (sys->n_csr_blocks > 0) {
-    if (sys->value_type == MC_VAL_F16) stream_fwd_launch<__half, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
-    else if (sys->value_type == MC_VAL_BF16)
+    if (value_storage(sys->value_type) == 1) stream_fwd_launch<__half, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
+    else if (value_storage(sys->value_type) == 2)
       stream_fwd_launch<__nv_bfloat16, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
     else stream_fwd_launch<float, MODE, LL>(sys, xs, y, out, partials, s, rmap, add);
     return;
   }
   const int g = sys->spmv_group_fwd;
-  if (sys->value_type == MC_VAL_F16) fwd_launch<__half, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
-  else if (sys->value_type == MC_VAL_BF16) fwd_launch<__nv_bfloat16, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
+  if (value_storage(sys->value_type) == 1) fwd_launch<__half, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
+  else if (value_storage(sys->value_type) == 2) fwd_launch<__nv_bfloat16, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
   else fwd_launch<float, MODE, LL>(sys, g, xs, y, out, partials, s, rmap, add);
 }
 
 template <int MODE>
 static void back_dispatch(const mc_system *sys, const float *r, float *x, float *xs, cudaStream_t s) {
   if (sys->n_csc_blocks > 0) {
-    if (sys->value_type == MC_VAL_F16) stream_back_launch<__half, MODE>(sys, r, x, xs, s);
-    else if (sys->value_type == MC_VAL_BF16) stream_back_launch<__nv_bfloat16, MODE>(sys, r, x, xs, s);
+    if (value_storage(sys->value_type) == 1) stream_back_launch<__half, MODE>(sys, r, x, xs, s);
+    else if (value_storage(sys->value_type) == 2) stream_back_launch<__nv_bfloat16, MODE>(sys, r, x, xs, s);
     else stream_back_launch<float, MODE>(sys, r, x, xs, s);
     return;
   }
   const int g = sys->spmv_group_bwd;
-  if (sys->value_type == MC_VAL_F16) back_launch<__half, MODE>(sys, g, r, x, xs, s);
-  else if (sys->value_type == MC_VAL_BF16) back_launch<__nv_bfloat16, MODE>(sys, g, r, x, xs, s);
+  if (value_storage(sys->value_type) == 1) back_launch<__half, MODE>(sys, g, r, x, xs, s);
+  else if (value_storage(sys->value_type) == 2) back_launch<__nv_bfloat16, MODE>(sys, g, r, x, xs, s);
   else back_launch<float, MODE>(sys, g, r, x, xs, s);
 }
 
@@ -606,6 +609,33 @@ static int stream_tiles(const DevBuf &ptr, int64_t n, int64_t nnz, DevBuf &tiles
   return MC_OK;
 }
 
+// Forced projector layouts (mc_system_set_spmv_layout): 0 = streaming
+// tiles (made now if the system has none), 1..32 = lanes per row group,
+// -1 = keep.  On an error the system keeps its previous layout.
+int set_spmv_layout(mc_system *sys, int fwd, int bwd, cudaStream_t s) {
+  auto ok = [](int g) { return g == -1 || g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; };
+  if (!ok(fwd) || !ok(bwd)) {
+    set_error("layouts must be -1 (keep), 0 (streaming tiles) or 1, 2, 4, 8, 16, 32 lanes; got %d, %d", fwd, bwd);
+    return MC_EINVAL;
+  }
+  DevBuf ft, bt;
+  int64_t nft = 0, nbt = 0;
+  bool fw = sys->warp_rows_fwd, bw = sys->warp_rows_bwd;
+  if (fwd == 0 && sys->n_csr_blocks == 0)
+    MCS_TRY(stream_tiles(sys->row_ptr, sys->n_rows, sys->nnz, ft, nft, fw, s, true));
+  if (bwd == 0 && sys->n_csc_blocks == 0)
+    MCS_TRY(stream_tiles(sys->col_ptr, sys->n_cols, sys->nnz, bt, nbt, bw, s, true));
+  if (fwd == 0 && sys->n_csr_blocks == 0) { sys->csr_blocks = std::move(ft); sys->n_csr_blocks = nft; sys->warp_rows_fwd = fw; }
+  if (bwd == 0 && sys->n_csc_blocks == 0) { sys->csc_blocks = std::move(bt); sys->n_csc_blocks = nbt; sys->warp_rows_bwd = bw; }
+  if (fwd > 0) { sys->n_csr_blocks = 0; sys->spmv_group_fwd = fwd; }
+  if (bwd > 0) { sys->n_csc_blocks = 0; sys->spmv_group_bwd = bwd; }
+  // the log-likelihood partials must cover the forward blocks of the layout
+  const int fb = forward_blocks(sys);
+  if ((size_t)fb * sizeof(double) > sys->partials.bytes) MCS_TRY(sys->partials.alloc((size_t)fb * sizeof(double), s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
 int make_stream_blocks(mc_system *sys, cudaStream_t s) {
   MCS_TRY(stream_tiles(sys->row_ptr, sys->n_rows, sys->nnz, sys->csr_blocks, sys->n_csr_blocks, sys->warp_rows_fwd, s));
   MCS_TRY(stream_tiles(sys->col_ptr, sys->n_cols, sys->nnz, sys->csc_blocks, sys->n_csc_blocks, sys->warp_rows_bwd, s));
@@ -614,7 +644,7 @@ int make_stream_blocks(mc_system *sys, cudaStream_t s) {
 
 int project(const mc_system *sys, const float *x, float *q, cudaStream_t s) {
   if (sys->n_cols > 0) {
-    count_launch(); prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
+    count_launch(); prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, proj_scale(sys), sys->xs.as<float>(),
                                                                      sys->n_cols);
   }
   if (sys->n_rows > 0) fwd_dispatch<0, false>(sys, sys->xs.as<float>(), nullptr, q, nullptr, s);
@@ -626,7 +656,7 @@ int project(const mc_system *sys, const float *x, float *q, cudaStream_t s) {
 int project_ratio(const mc_system *sys, const float *x, const float *y, float *r, cudaStream_t s) {
   if (sys->n_cols > 0) {
     count_launch();
-    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
+    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, proj_scale(sys), sys->xs.as<float>(),
                                                                      sys->n_cols);
   }
   if (sys->n_rows > 0) fwd_dispatch<1, false>(sys, sys->xs.as<float>(), y, r, nullptr, s);
@@ -638,7 +668,7 @@ int project_ratio(const mc_system *sys, const float *x, const float *y, float *r
 int loglik(const mc_system *sys, const float *x, const float *y, double *value, cudaStream_t s) {
   if (sys->n_cols > 0) {
     count_launch();
-    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(),
+    prescale_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x, proj_scale(sys), sys->xs.as<float>(),
                                                                      sys->n_cols);
   }
   if (sys->n_rows > 0) {
@@ -660,8 +690,9 @@ int backproject(const mc_system *sys, const float *r, float *b, cudaStream_t s) 
 
 int sensitivity(const mc_system *sys, double *out, cudaStream_t s) {
   if (sys->n_cols > 0) {
-    count_launch(); sensitivity_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(sys->colsum.as<double>(),
-                                                                       sys->n_v.as<uint32_t>(), sys->n_cols, out);
+    const uint32_t *nv = nullptr;
+    const double *cs = proj_sens_terms(sys, &nv);
+    count_launch(); sensitivity_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(cs, nv, sys->n_cols, out);
   }
   MCS_LAUNCHED();
   return MC_OK;
@@ -672,16 +703,16 @@ int mlem_init(mc_system *sys, const float *y, float *x, cudaStream_t s) {
   DevBuf part;
   MCS_TRY(part.alloc((2 * nb + 1) * sizeof(double), s));
   double *py = part.as<double>(), *ps = py + nb, *x0 = py + 2 * nb;
+  const uint32_t *nv = nullptr;
+  const double *cs = proj_sens_terms(sys, &nv);
   count_launch();
-  init_sums_kernel<<<nb, 256, 0, s>>>(y, sys->n_rows, sys->colsum.as<double>(), sys->n_v.as<uint32_t>(), sys->n_cols,
-                                      py, ps);
+  init_sums_kernel<<<nb, 256, 0, s>>>(y, sys->n_rows, cs, nv, sys->n_cols, py, ps);
   count_launch();
   init_total_kernel<<<1, 256, 0, s>>>(py, ps, nb, x0);
   MCS_LAUNCHED();
   if (sys->n_cols > 0) {
     count_launch();
-    init_fill_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x0, sys->colsum.as<double>(),
-                                                                     sys->inv_n.as<float>(), sys->n_cols, x,
+    init_fill_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(x0, cs, proj_scale(sys), sys->n_cols, x,
                                                                      sys->xs.as<float>());
   }
   MCS_LAUNCHED();
@@ -701,7 +732,7 @@ int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const flo
       const int64_t n = f->n_cols;
       if (n > 0) {
         count_launch();
-        prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, f->inv_n.as<float>(), f->xs.as<float>(), n);
+        prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, proj_scale(f), f->xs.as<float>(), n);
       }
       if (f->n_rows > 0)
         fwd_dispatch<2, false>(f, f->xs.as<float>(), y, f->r.as<float>(), nullptr, s,
@@ -716,7 +747,7 @@ int osem_run(mc_system *const *fwd, mc_system *const *back, int n_sub, const flo
 int mlem_run(mc_system *sys, const float *y, float *x, int n_iter, bool want_ll, cudaStream_t s) {
   const int64_t m = sys->n_rows, n = sys->n_cols;
   if (n > 0) {
-    count_launch(); prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, sys->inv_n.as<float>(), sys->xs.as<float>(), n);
+    count_launch(); prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x, proj_scale(sys), sys->xs.as<float>(), n);
   }
   MCS_LAUNCHED();
   const int fb = forward_blocks(sys);
@@ -821,7 +852,7 @@ extern "C" int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, fl
   // every scratch element is written before it is read: nothing to clear
   if (n > 0) {
     count_launch();
-    prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x_dev, sys->inv_n.as<float>(), xs, n);
+    prescale_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(x_dev, proj_scale(sys), xs, n);
   }
   MCS_LAUNCHED();
   for (int k = 0; k < n_iter; ++k) {

@@ -22,7 +22,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmcspect.so")
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA = 0, -1, -2, -3
 MC_FP32, MC_FP64 = 0, 1
-MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16 = 0, 1, 2
+MC_VAL_F32, MC_VAL_F16, MC_VAL_BF16, MC_VAL_F16_A, MC_VAL_BF16_A = 0, 1, 2, 3, 4
+VALUE_TYPES = {"f32": MC_VAL_F32, "f16": MC_VAL_F16, "bf16": MC_VAL_BF16, "f16_a": MC_VAL_F16_A,
+               "bf16_a": MC_VAL_BF16_A}
 MC_TALLY_ALL, MC_TALLY_PRIMARY, MC_TALLY_FORCED, MC_TALLY_FORCED_DIRECTION = 0, 1, 2, 4
 FD_SCALE = 2.0 ** 48  # forced-detection weights are tallied as rint(w * 2^48)
 FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
@@ -31,7 +33,7 @@ FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 EXPORTED = (
     "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events",
     "mc_system_from_weighted_events", "mc_system_export_values", "mc_system_free",
-    "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type",
+    "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type", "mc_system_set_spmv_layout",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
     "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
     "mc_prior_quadratic_f64", "mc_pgd_step", "mc_system_autotune", "mc_batch_create", "mc_batch_mlem",
@@ -125,6 +127,7 @@ def load(path: str | None = None):
             "mc_prior_quadratic_f64": [i32, i32, i32, dbl, vp, vp, vp, vp],
             "mc_pgd_step": [i64, dbl, vp, vp, vp, vp, vp],
             "mc_system_autotune": [vp, vp],
+            "mc_system_set_spmv_layout": [vp, i32, i32, vp],
             "mc_batch_create": [vp, i32, vp, vp, vp],
             "mc_batch_mlem": [vp, i32, vp],
             "mc_batch_free": [vp],
@@ -252,7 +255,7 @@ class System:
         return a[:n], b[:n]
 
     def set_value_type(self, value_type, allow_rounding=False):
-        vt = {"f32": MC_VAL_F32, "f16": MC_VAL_F16, "bf16": MC_VAL_BF16}.get(value_type, value_type)
+        vt = VALUE_TYPES.get(value_type, value_type)
         _check(load().mc_system_set_value_type(self.handle, int(vt), int(bool(allow_rounding))))
 
     def free(self):
@@ -473,6 +476,14 @@ def mc_pgd_step(alpha: float, sens, bp, x, gp=None, stream=None):
                               _dev_ptr(bp, torch.float32), _dev_ptr(gp, torch.float32) if gp is not None else None,
                               _dev_ptr(x, torch.float32), _stream_ptr(stream)))
     return x
+
+
+def mc_system_set_spmv_layout(sys: System, fwd: int, bwd: int, stream=None):
+    """Projector layouts: 0 streaming tiles, 1..32 lanes per row (column)
+    group, -1 keep; returns the layouts now in use."""
+    _check(load().mc_system_set_spmv_layout(sys.handle, int(fwd), int(bwd), _stream_ptr(stream)))
+    i = sys.info()
+    return i["spmv_fwd"], i["spmv_bwd"]
 
 
 def mc_system_autotune(sys: System, stream=None):

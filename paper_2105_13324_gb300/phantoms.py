@@ -301,3 +301,39 @@ def segments16(phantom: Phantom) -> np.ndarray:
     half = (z >= c[2]).astype(np.int64)
     seg = sector * 2 + half
     return np.where(heart, seg, -1)
+
+
+def random_events(n_rows: int, n_cols: int, row_len: tuple[int, int], count_max: int, seed: int,
+                  rows_used: float = 1.0):
+    """Synthetic tally events (row j, column v) of a sparse count matrix, for
+    projector and ML-EM tests at chosen row lengths and count ranges.  A
+    fraction ``rows_used`` of the rows (chosen at random) holds entries; each
+    such row gets a length uniform in ``row_len`` (clipped to n_cols) of
+    distinct random columns, each entry a count uniform in 1..count_max
+    (repeated events).  Seeded with numpy's Philox generator; returns int32
+    rows and cols in random order."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    used = np.flatnonzero(rng.random(n_rows) < rows_used)
+    lens = np.minimum(rng.integers(row_len[0], row_len[1] + 1, len(used)), n_cols)
+    rows = np.repeat(used, lens)
+    # distinct columns within each row
+    cols = np.empty(len(rows), np.int64)
+    pos = 0
+    for ln in lens:
+        cols[pos:pos + ln] = rng.choice(n_cols, ln, replace=False)
+        pos += ln
+    cnt = rng.integers(1, count_max + 1, len(rows))
+    r = np.repeat(rows, cnt).astype(np.int32)
+    c = np.repeat(cols, cnt).astype(np.int32)
+    order = rng.permutation(len(r))
+    return r[order], c[order]
+
+
+def uniform_events(n_rows: int, n_cols: int, n_events: int, seed: int):
+    """Synthetic tally events with row and column independent and uniform
+    (repeated pairs add up to counts): a sparse count matrix of any size
+    with short rows, e.g. the size class of a 128^3, 120-view system.
+    Seeded with numpy's Philox generator; int32 rows and cols."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return (rng.integers(0, n_rows, n_events).astype(np.int32),
+            rng.integers(0, n_cols, n_events).astype(np.int32))
