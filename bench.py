@@ -10,8 +10,10 @@ steps.  Printed as one JSON line.
 
 --impl reference times the CPU oracle (the FP64 C transport + tally) on the
 host cores on a bounded sample of the same workload.  With N > 1 (torchrun)
-every rank reconstructs its own acquisition (its own seed): independent
-problems, no collective on the data path, weak scaling.
+the ranks split one acquisition of N x H histories: history ranges per rank,
+events routed to the rank owning their view, ML-EM rows by views with one
+all-reduce per iteration (weak scaling); --replicas gives every rank its own
+acquisition instead (no collective on the data path).
 """
 from __future__ import annotations
 
@@ -232,7 +234,11 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "histories_per_step": hs,
-                                            "note": "CPU oracle on a bounded history sample per step"},
+                                            "step": "transport + tally only (no ML-EM)",
+                                            "note": "CPU oracle on a bounded history sample per step; the GPU "
+                                                    "step also runs 50 ML-EM iterations, which the oracle's "
+                                                    "ML-EM rate on the benchmark matrix is reported for in the "
+                                                    "GPU line (reduced_precision.oracle_mlem_iter_per_s)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{hs} histories per step of the {w.name} workload, transport + tally"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -372,6 +378,119 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
     return out
 
 
+def _segment_means(img, seg):
+    """Mean image value in each of the 16 myocardial segments."""
+    return np.array([img[seg == k].mean() if np.any(seg == k) else 0.0 for k in range(16)])
+
+
+def reduced_precision_benchmark(mc, system, y_host, w, n_iter, flush, stream):
+    """N1: ML-EM images with the matrix values stored in each type against
+    the FP64 oracle image on the same matrix and projections (relative L2
+    over the image and the 16 myocardial segment means), with ms per
+    iteration.  f32 / f16 / bf16 store the counts (exact here: the largest
+    count is far below 256); f16_a / bf16_a store A = C / n_v itself,
+    rounded (the conventional reduced-precision storage).  The oracle's
+    float64 ML-EM runs on the CPU on the benchmark matrix exported from the
+    device, timed as the oracle's ML-EM rate on this matrix.  A synthetic
+    count matrix with counts up to 6000 (oracle-built) shows the rounding of
+    counts beyond the exact range of half / bfloat16."""
+    import torch
+
+    import oracle
+    M, N = system.shape
+    cp, ri, cnt, nv = system.export_csc()
+    c = sp_csc(cnt, ri, cp, (M, N))
+    a = oracle.system_matrix(c, nv)
+    y = np.asarray(y_host, np.float64)
+    t0 = time.perf_counter()
+    x_o = oracle.mlem(a, y, oracle.mlem_init(a, y), n_iter)
+    oracle_s = time.perf_counter() - t0
+    seg = P.segments16(w.phantom).ravel()
+    seg_o = _segment_means(x_o, seg)
+    yd = torch.as_tensor(np.asarray(y_host, np.float32)).cuda()
+    x = torch.zeros(N, dtype=torch.float32, device="cuda")
+    out = {"matrix": f"benchmark matrix ({M} x {N}, nnz {c.nnz}, largest count {int(cnt.max()) if cnt.size else 0})",
+           "mlem_iters": n_iter, "oracle": "float64 ML-EM (CPU, scipy) on the exported matrix and the same y",
+           "oracle_mlem_iter_per_s": n_iter / oracle_s, "types": {}}
+    for vt in ("f32", "f16", "bf16", "f16_a", "bf16_a"):
+        system.set_value_type(vt)
+        t = mlem_timing(mc, system, yd, x, n_iter, flush, stream, label=vt)[vt]
+        mc.mc_mlem_init(system, yd, x)
+        mc.mlem_iterate(system, yd, x, n_iter)
+        img = x.cpu().numpy().astype(np.float64)
+        seg_g = _segment_means(img, seg)
+        t["rel_l2_vs_oracle"] = float(np.linalg.norm(img - x_o) / np.linalg.norm(x_o))
+        t["segment_mean_rel_err_max"] = float(np.max(np.abs(seg_g - seg_o) / np.abs(seg_o)))
+        t["segment_mean_rel_err_mean"] = float(np.mean(np.abs(seg_g - seg_o) / np.abs(seg_o)))
+        out["types"][vt] = t
+    system.set_value_type("f32")
+    # counts beyond the exact range (synthetic, oracle-built): 128 x 256
+    n_rows, n_cols, H = 128, 256, 5 * 256
+    rows, cols = P.random_events(n_rows, n_cols, (10, 30), 6000, seed=31)
+    cs = oracle.system_counts(rows, cols, n_rows, n_cols)
+    a_s = oracle.system_matrix(cs, oracle.histories_per_voxel(n_cols, 0, H))
+    y_s = P.poisson_counts(a_s @ np.ones(n_cols), 50.0 * n_rows, 32)
+    want = oracle.mlem(a_s, y_s, oracle.mlem_init(a_s, y_s), 20)
+    s_syn = mc.mc_system_from_events(n_rows, n_cols, rows, cols, 0, H)
+    ys = torch.as_tensor(y_s).cuda()
+    hc = {"matrix": f"synthetic {n_rows} x {n_cols} counts 1..6000 (oracle-built), 20 iterations"}
+    for vt in ("f32", "f16", "bf16"):
+        s_syn.set_value_type(vt, allow_rounding=True)
+        xs = torch.zeros(n_cols, dtype=torch.float32, device="cuda")
+        mc.mc_mlem_init(s_syn, ys, xs)
+        mc.mlem_iterate(s_syn, ys, xs, 20)
+        hc[vt + "_rel_l2_vs_oracle"] = float(np.linalg.norm(xs.cpu().numpy() - want) / np.linalg.norm(want))
+    s_syn.free()
+    out["high_counts"] = hc
+    return out, a, x_o
+
+
+def sp_csc(data, indices, indptr, shape):
+    import scipy.sparse as sp
+    return sp.csc_matrix((np.asarray(data, np.int64), indices, indptr), shape=shape)
+
+
+def penalised_benchmark(mc, system, y_host, a, w, n_iter, stream):
+    """N2: the penalised Poisson likelihood solved by EM-preconditioned
+    gradient steps through the library (paper Sec. 5.1 likelihood plus a
+    quadratic 6-neighbour prior; beta relative to the mean sensitivity),
+    against plain FP32 ML-EM on the same matrix: ms per iteration, the final
+    objective against the oracle's float64 objective of the same image, and
+    the image's relative L2 to the ML-EM image."""
+    import torch
+
+    import oracle
+    from paper_2105_13324_gb300 import autograd as AG
+    M, N = system.shape
+    yd = torch.as_tensor(np.asarray(y_host, np.float32)).cuda()
+    x_em = torch.zeros(N, dtype=torch.float32, device="cuda")
+    mc.mc_mlem_init(system, yd, x_em)
+    mc.mlem_iterate(system, yd, x_em, n_iter)
+    em = x_em.cpu().numpy().astype(np.float64)
+    sens = torch.zeros(N, dtype=torch.float64, device="cuda")
+    mc.mc_sensitivity(system, sens)
+    s_mean = float(sens.mean())
+    shape = w.phantom.shape
+    y = np.asarray(y_host, np.float64)
+    out = {"iters": n_iter, "beta_basis": f"beta = rel x mean sensitivity ({s_mean:.4g})", "runs": {}}
+    for rel in (0.0, 1e-4, 1e-3, 1e-2, 1e-1):
+        beta = rel * s_mean
+        hist = []
+        AG.penalised_reconstruct(system, yd, shape, beta, 2)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = AG.penalised_reconstruct(system, yd, shape, beta, n_iter, history=hist)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        img = x.cpu().numpy().astype(np.float64)
+        phi_o = oracle.penalised_objective(a, y, img, shape, beta)
+        out["runs"][f"{rel:g}"] = {"beta": beta, "ms_per_iter": 1e3 * dt / n_iter,
+                                   "phi": hist[-1], "phi_oracle": phi_o,
+                                   "phi_rel_diff": float(abs(hist[-1] - phi_o) / abs(phi_o)),
+                                   "rel_l2_vs_mlem": float(np.linalg.norm(img - em) / np.linalg.norm(em))}
+    return out
+
+
 def _blocks(q, geometry, b=8):
     # projection (views x bins_v x bins_u) summed over b x b bins
     V, bv, bu = geometry.n_views, geometry.n_bins_v, geometry.n_bins_u
@@ -446,6 +565,121 @@ def fd_benchmark(mc, w, analog, analog_ms, seed, n_batches, stream):
     return out
 
 
+def run_split(args, w):
+    """N > 1 ranks (torchrun, one GPU each, NCCL): one acquisition of
+    N x H histories split over the ranks (paper_2105_13324_gb300.sharded).
+    Rank g runs histories [g N H / N, ...), routes its events to the rank
+    owning their view (one all-to-all), assembles the rows of its views, and
+    ML-EM runs with one all-reduce of the N-voxel back-projection per
+    iteration.  Work per rank is fixed as N grows: weak scaling."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2105_13324_gb300 import build as B
+    from paper_2105_13324_gb300 import mcspect as mc
+    from paper_2105_13324_gb300 import sharded
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init_process_group("nccl", device_id=dev)
+    mc.load(B.build())
+    H = int(args.histories or w.n_histories)
+    total = ws * H
+    n_iter = int(args.mlem_iters or w.mlem_iters)
+    g = w.geometry
+    rpv = g.n_bins_u * g.n_bins_v
+    M, N = g.n_views * rpv, int(np.prod(w.phantom.shape))
+    comm, ops = sharded.TorchComm(), sharded.LibraryOps(mc)
+    stream = torch.cuda.current_stream()
+    plan = mc.Plan(w.phantom, g, "fp32")
+    # projections of this rank's views: an independent realisation (seed +
+    # 1000) projects the activity; Poisson counts at the workload's total x N
+    truth, (v0, v1) = sharded.split_build(ops, comm, plan, M, N, rpv, total, w.seed + 1000)
+    m_p = (v1 - v0) * rpv
+    ybar = torch.zeros(m_p, dtype=torch.float32, device=dev)
+    mc.mc_project(truth, torch.as_tensor(w.phantom.activity.ravel()).to(dev), ybar)
+    truth.free()
+    tot = torch.tensor([float(ybar.double().sum())], dtype=torch.float64, device=dev)
+    part = float(tot[0])
+    dist.all_reduce(tot)
+    y_host = P.poisson_counts(ybar.cpu().numpy(), w.total_counts * ws * part / max(float(tot[0]), 1e-300),
+                              w.noise_seed + rank)
+    y = torch.as_tensor(y_host).to(dev)
+    flush = torch.empty(int(args.flush_mb) * (1 << 20) // 4, dtype=torch.float32, device=dev)
+
+    def step(y_part):
+        s, _ = sharded.split_build(ops, comm, plan, M, N, rpv, total, w.seed)
+        x = sharded.split_mlem(ops, comm, s, y_part, m_p, N, n_iter)
+        return s, x
+
+    for _ in range(args.warmup):
+        step(y)[0].free()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    l0 = mc.mc_kernel_launches()
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        s, x = step(y)
+        ev[k][1].record(stream)
+        infos.append(s.info())
+        s.free()
+    torch.cuda.synchronize()
+    launches = mc.mc_kernel_launches() - l0
+    dist.barrier()
+    clk = clocks.stop()
+    ms = _maxreduce(float(np.mean([a.elapsed_time(b) for a, b in ev])), ws, dev)
+    # end to end: y from pinned host memory each step, the image read back
+    y_pin = torch.as_tensor(y_host).pin_memory()
+    x_pin = torch.empty(N, dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        y_dev.copy_(y_pin, non_blocking=True)
+        s, x = step(y_dev)
+        x_pin.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        s.free()
+    e2e_ms = _maxreduce(float(np.mean(e2e_ms)), ws, dev)
+    if rank == 0:
+        inf = infos[-1]
+        line = {
+            "metric": METRIC, "value": total / (ms * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.phantom.shape), "views": g.n_views,
+                       "bins": [g.n_bins_v, g.n_bins_u], "histories_per_step": total, "histories_per_rank": H,
+                       "mlem_iters": n_iter, "l2": f"flushed ({args.flush_mb} MB write) between timed steps",
+                       "parallelism": f"split over {ws} GPUs: history ranges per rank, events routed to the rank "
+                                      "owning their view (one all-to-all), ML-EM rows by views with one all-reduce "
+                                      "of the N-voxel back-projection per iteration"},
+            "rank0_part": {"views": [v0, v1], "rows": m_p, "nnz": inf["nnz"],
+                           "build_ms_transport": inf["build_ms_transport"]},
+            "clocks": clk,
+            "e2e": {"value": total / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(4 * m_p),
+                    "d2h_bytes_per_step": int(4 * N)},
+            "gpu_launches": int(launches),
+            "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    plan.free()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args, w):
     import torch
 
@@ -518,32 +752,17 @@ def run_ours(args, w):
     ms = _maxreduce(float(np.mean(step_ms)), ws, dev)
     value = whole_job_rate(ws, H, ms)
 
-    # ML-EM alone on the last system: iterations/s per value type
+    # ML-EM alone on the last system
     inf = infos[-1]
     hbm_gbs, sm_max_mhz, peak_kind = _peaks()
     mlem = mlem_timing(mc, last, y, x, n_iter, flush, stream)
     it_ms = mlem["f32"]["ms_per_iter"]
-    value_types = {}
-    x32 = None
-    for vt in ("f32", "f16", "bf16"):
-        if vt != "f32":
-            limit = 2048 if vt == "f16" else 256
-            if inf["max_count"] > limit:
-                value_types[vt] = {"skipped": f"counts up to {inf['max_count']} not exact"}
-                continue
-            last.set_value_type(vt)
-            t = mlem_timing(mc, last, y, x, n_iter, flush, stream, label=vt)[vt]
-        else:
-            t = mlem[vt]
-        mc.mc_mlem_init(last, y, x)
-        mc.mlem_iterate(last, y, x, n_iter)
-        img = x.cpu().numpy().astype(np.float64)
-        if vt == "f32":
-            x32 = img
-        t["rel_l2_vs_f32"] = float(np.linalg.norm(img - x32) / max(np.linalg.norm(x32), 1e-300))
-        value_types[vt] = t
-    last.set_value_type("f32")
     mlem_bytes = spmv_bytes(last, inf["nnz"], M, N, 4)
+    reduced = penalised = None
+    if rank == 0 and not args.no_oracle_images:
+        reduced, a_bench, _ = reduced_precision_benchmark(mc, last, y_host, w, n_iter, flush, stream)
+        penalised = penalised_benchmark(mc, last, y_host, a_bench, w, int(args.penalised_iters), stream)
+        del a_bench
 
     # SpMV roofline on a matrix larger than L2 (same geometry, more histories)
     roof = None
@@ -601,6 +820,10 @@ def run_ours(args, w):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, target_s=args.cpu_seconds)
+        if reduced is not None:
+            # the oracle's float64 ML-EM on the benchmark matrix itself (one
+            # thread, scipy), beside the GPU's iterations/s on the same matrix
+            cpu["mlem_iter_per_s_benchmark_matrix"] = reduced["oracle_mlem_iter_per_s"]
 
     if rank == 0:
         line = {
@@ -639,7 +862,8 @@ def run_ours(args, w):
             "roofline_mlem_roof": roof,
             "serving": serving,
             "forced_detection": fd,
-            "mlem_value_types": value_types,
+            "reduced_precision": reduced,
+            "penalised": penalised,
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -672,10 +896,19 @@ def main(argv=None):
                     help="forced-detection builds of one history per voxel each (0: skip)")
     ap.add_argument("--roof-histories", type=float, default=1e11,
                     help="histories of the large-matrix SpMV roofline instance (0: skip)")
+    ap.add_argument("--no-oracle-images", action="store_true",
+                    help="skip the value-type and penalised-solver comparisons with the oracle's images")
+    ap.add_argument("--penalised-iters", type=int, default=20)
+    ap.add_argument("--split", action="store_true",
+                    help="run the split path even on one rank (under torchrun; checks the multi-GPU code path)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 ranks: independent acquisitions per rank instead of one split acquisition")
     args = ap.parse_args(argv)
     w = P.workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
+    if (_dist()[0] > 1 and not args.replicas) or args.split:
+        return run_split(args, w)
     return run_ours(args, w)
 
 

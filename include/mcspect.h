@@ -191,6 +191,39 @@ MC_API int mc_plan_build(mc_plan *plan, uint64_t first, uint64_t count, uint64_t
 /* Release a plan (NULL is accepted). */
 MC_API int mc_plan_free(mc_plan *plan);
 
+/* The tally of a history range without assembly (Sec. 2 transport, the
+ * detections that estimate T_ij of Eq. (IMC), Sec. 5.1): the events of
+ * histories first .. first+count-1 of the plan, one key v * M + j per
+ * detection (row j, voxel v, M = the plan's rows), in no fixed order, into
+ * the caller's device buffer keys_dev[capacity].  *n_events_out receives
+ * the number of events and fates_host[4] (nullable) the history fates.  The
+ * tally is deterministic: if it does not fit (MC_EINVAL, *n_events_out set)
+ * repeat the call with a larger buffer.  MC_EINVAL for weighted plans
+ * (forced detection or forced direction).  Synchronises `stream`. */
+MC_API int mc_plan_tally(mc_plan *plan, uint64_t first, uint64_t count, uint64_t seed, uint64_t *keys_dev,
+                         int64_t capacity, int64_t *n_events_out, uint64_t *fates_host, void *stream);
+
+/* Routing of tally events to the parts of a view-partitioned system (the
+ * split of one reconstruction over several GPUs; the back-projection sum of
+ * Eq. (MLEM) runs over detector bins, so bins split by views).  The
+ * n_rows / rows_per_view views are cut into n_parts contiguous blocks, part
+ * p holding views [p V / n_parts, (p + 1) V / n_parts) (integer division).
+ * keys_dev[n_events] (v * n_rows + j) are written to out_dev[n_events]
+ * grouped by part (part 0 first; no fixed order inside a part), each key
+ * renumbered to its part's rows: v * M_p + (j - first row of part p), M_p =
+ * the part's views x rows_per_view.  part_counts_host[n_parts] receives the
+ * events per part.  MC_EINVAL if n_rows is not a multiple of rows_per_view
+ * or n_parts is not in 1 .. min(views, 1024).  Synchronises `stream`. */
+MC_API int mc_events_route(const uint64_t *keys_dev, int64_t n_events, int64_t n_rows, int64_t rows_per_view,
+                           int32_t n_parts, uint64_t *out_dev, int64_t *part_counts_host, void *stream);
+
+/* Matrix from device event keys v * n_rows + j (duplicates add), e.g. the
+ * routed events of one part; n_v is that of the history range [first,
+ * first+count).  The caller's keys are not modified.  MC_EINVAL for a key
+ * >= n_rows * n_cols.  Synchronises `stream`. */
+MC_API int mc_system_from_keys(int64_t n_rows, int64_t n_cols, const uint64_t *keys_dev, int64_t n_keys,
+                               uint64_t first, uint64_t count, void *stream, mc_system **out);
+
 /* As mc_build_system for histories first .. first+count-1 only (chunked or
  * resumed runs): the counts and n_v of disjoint ranges add up exactly to
  * those of their union. */
@@ -268,7 +301,9 @@ MC_API int mc_project_ratio(const mc_system *sys, const float *x_dev, const floa
 
 /* Poisson log-likelihood of Sec. 5.1 (up to a constant) of an image:
  * *value_dev = sum_j y_j ln q_j - q_j, q = A x, bins with y_j = 0 adding
- * -q_j; FP64 accumulation.  x_dev[N], y_dev[M] float; value_dev one double. */
+ * -q_j, and bins whose row of A is empty left out of the y_j ln q_j sum
+ * (q_j = 0 for every image there; ML-EM ignores them the same way);
+ * FP64 accumulation.  x_dev[N], y_dev[M] float; value_dev one double. */
 MC_API int mc_loglik(const mc_system *sys, const float *x_dev, const float *y_dev, double *value_dev, void *stream);
 
 /* Back-projection b = A^T r: r_dev[M], b_dev[N], float. */
@@ -281,12 +316,23 @@ MC_API int mc_sensitivity(const mc_system *sys, double *s_dev, void *stream);
 /* Uniform start image: x_v = sum(y) / sum(s) where s_v > 0, else 0. */
 MC_API int mc_mlem_init(mc_system *sys, const float *y_dev, float *x_dev, void *stream);
 
+/* Pieces of ML-EM over a system split into parts (each part holding some
+ * detector rows, Eq. (MLEM) summing over them): the FP64 sum of a float
+ * vector (*out_dev = sum of v_dev[n], fixed order), and the uniform start
+ * image from a sensitivity summed over the parts: x_v = sum_y / sum(sens)
+ * where sens_v > 0, else 0 (sens_dev[n] double, x_dev[n] float).  The
+ * update x_v <- x_v b_v / s_v from a back-projection summed over the parts
+ * is mc_pgd_step with alpha = 1 and no prior. */
+MC_API int mc_vector_sum(int64_t n, const float *v_dev, double *out_dev, void *stream);
+MC_API int mc_mlem_start(int64_t n, const double *sens_dev, double sum_y, float *x_dev, void *stream);
+
 /* n_iter ML-EM updates of Eq. (MLEM), in place on x_dev[N]:
  *   x_v <- x_v / s_v * sum_j A_jv y_j / (A x)_j,
  * with y_j / (A x)_j taken as 0 where (A x)_j = 0 and x_v = 0 where s_v = 0.
  * If loglik_host is not NULL it receives n_iter values
- * L(x^k) = sum_j y_j ln q_j - q_j (FP64; bins with y_j = 0 add -q_j) for
- * the iterates before each update, and the call synchronises `stream`. */
+ * L(x^k) = sum_j y_j ln q_j - q_j (FP64; bins with y_j = 0 add -q_j, bins
+ * with an empty row are left out of the log term, as in mc_loglik) for the
+ * iterates before each update, and the call synchronises `stream`. */
 MC_API int mlem_iterate(mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter, double *loglik_host,
                  void *stream);
 

@@ -387,12 +387,20 @@ def mlem_init(a: sp.spmatrix, y: np.ndarray) -> np.ndarray:
     return x
 
 
+def reached_bins(a: sp.spmatrix) -> np.ndarray:
+    """Bins whose row of A holds an entry: the bins the model can reach."""
+    return np.diff(sp.csr_matrix(a).indptr) > 0
+
+
 def loglik(a: sp.spmatrix, x: np.ndarray, y: np.ndarray) -> float:
     """Poisson log-likelihood without the constant: sum_j y_j ln q_j - q_j,
-    q = A x; bins with y_j = 0 contribute -q_j only."""
+    q = A x; bins with y_j = 0 contribute -q_j only.  A bin whose row of A is
+    empty is left out of the y_j ln q_j sum: q_j = 0 for every image, so the
+    term carries no information about x (it would be -inf whatever x is),
+    and ML-EM ignores the bin the same way (r_j = 0 where (A x)_j = 0)."""
     q = a @ np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
-    pos = y > 0
+    pos = (y > 0) & reached_bins(a)
     with np.errstate(divide="ignore"):
         return float(np.sum(y[pos] * np.log(q[pos])) - np.sum(q))
 
@@ -483,11 +491,13 @@ def prior_quadratic(x: np.ndarray, shape, beta: float):
 
 def penalised_objective(a: sp.spmatrix, y: np.ndarray, x: np.ndarray, shape, beta: float) -> float:
     """sum_j (q_j - y_j ln q_j) + R(x), q = A x (negative log-likelihood up to
-    a constant, plus the prior)."""
+    a constant, plus the prior); bins with an empty row of A are left out of
+    the y_j ln q_j sum, as in ``loglik``."""
     q = a @ np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
-    pos = y > 0
-    return float(np.sum(q) - np.sum(y[pos] * np.log(q[pos])) + prior_quadratic(x, shape, beta)[0])
+    pos = (y > 0) & reached_bins(a)
+    with np.errstate(divide="ignore"):
+        return float(np.sum(q) - np.sum(y[pos] * np.log(q[pos])) + prior_quadratic(x, shape, beta)[0])
 
 
 def penalised_gradient(a: sp.spmatrix, y: np.ndarray, x: np.ndarray, shape, beta: float) -> np.ndarray:

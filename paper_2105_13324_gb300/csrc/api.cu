@@ -90,6 +90,8 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
 int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s);
 void batch_free(mc_batch *b);
 int autotune(mc_system *sys, cudaStream_t s, int *fwd_choice, int *bwd_choice);
+int vector_sum(int64_t n, const float *v, double *out, cudaStream_t s);
+int mlem_start(int64_t n, const double *sens, double sum_y, float *x, cudaStream_t s);
 void compute_coefficients(const TransportSetup &ts, std::vector<double> &cd, std::vector<float> &cf,
                           std::vector<float> &sig_tab);
 
@@ -329,8 +331,16 @@ __global__ void queue_reset_kernel(unsigned long long *ctr) {
   ctr[5] = 0ull;
 }
 
-static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
-                           mc_system **out) {
+// Result of the transport + detection part of a build (the tally, before
+// assembly): the event keys v M + j (and, weighted, the fixed-point weights),
+// the counters and the device times.
+struct Tally {
+  DevBuf events, weights;
+  unsigned long long hctr[kCounters] = {};
+  float ms_transport = 0.f, ms_detect = 0.f;
+};
+
+static int tally_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s, Tally &out) {
   if (count == 0) { set_error("no histories requested"); return MC_EINVAL; }
   if (first + count < first) { set_error("history range overflows 64 bits"); return MC_EINVAL; }
   TransportSetup ts = pl->ts;
@@ -338,13 +348,6 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
   ts.count = count;
   ts.key0 = (uint32_t)seed;
   ts.key1 = (uint32_t)(seed >> 32);
-  mc_system *sys = new (std::nothrow) mc_system();
-  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
-  auto fail = [&](int rc) { delete sys; return rc; };
-  sys->n_rows = (int64_t)ts.n_views * ts.bins_u * ts.bins_v;
-  sys->n_cols = (int64_t)ts.nx * ts.ny * ts.nz;
-  sys->first = first;
-  sys->count = count;
   int rc;
   // Histories run in chunks of kChunk: the escape queue is sized for one
   // chunk and reused, the events of all chunks accumulate.  Analog chunks
@@ -381,26 +384,22 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
                         : (double)chunk_max * (ts.forced_dir ? 1.0 : w_max * 1.1) + 65536.0;
   if (!forced && est_q > (double)chunk_max) est_q = (double)chunk_max;
   unsigned long long cap = (unsigned long long)est, cap_q = (unsigned long long)est_q;
-  DevBuf events, ctr, esc, weights;
-  std::vector<cudaEvent_t> evs(3 * n_chunks + 1, nullptr);
+  DevBuf ctr, esc;
+  std::vector<cudaEvent_t> evs(3 * n_chunks, nullptr);
   struct EvGuard {
     std::vector<cudaEvent_t> &v;
     ~EvGuard() { for (cudaEvent_t e : v) if (e) cudaEventDestroy(e); }
   } eg{evs};
   for (auto &e : evs)
-    if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return fail(MC_ECUDA); }
-  cudaEvent_t e_end = evs.back();
-  if ((rc = ctr.alloc(kCounters * sizeof(unsigned long long), s))) return fail(rc);
-  unsigned long long hctr[kCounters];
+    if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return MC_ECUDA; }
+  MCS_TRY(ctr.alloc(kCounters * sizeof(unsigned long long), s));
+  unsigned long long *hctr = out.hctr;
   for (int attempt = 0; attempt < 3; ++attempt) {
-    if ((rc = events.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
-    if (weighted && (rc = weights.alloc(cap * sizeof(unsigned long long), s))) return fail(rc);
-    if ((rc = esc.alloc(cap_q * qb, s))) return fail(rc);
-    if (cudaMemsetAsync(ctr.p, 0, kCounters * sizeof(unsigned long long), s) != cudaSuccess) {
-      set_error("cudaMemsetAsync failed");
-      return fail(MC_ECUDA);
-    }
-    ts.events = events.as<unsigned long long>();
+    MCS_TRY(out.events.alloc(cap * sizeof(unsigned long long), s));
+    if (weighted) MCS_TRY(out.weights.alloc(cap * sizeof(unsigned long long), s));
+    MCS_TRY(esc.alloc(cap_q * qb, s));
+    MCS_CUDA(cudaMemsetAsync(ctr.p, 0, kCounters * sizeof(unsigned long long), s));
+    ts.events = out.events.as<unsigned long long>();
     ts.capacity = cap;
     ts.cursor = ctr.as<unsigned long long>();
     ts.fates = ctr.as<unsigned long long>() + 1;
@@ -408,28 +407,28 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     ts.esc_capacity = cap_q;
     ts.esc_cursor = ctr.as<unsigned long long>() + 5;
     ts.records = nullptr;
-    ts.weights = weighted ? weights.as<unsigned long long>() : nullptr;
+    ts.weights = weighted ? out.weights.as<unsigned long long>() : nullptr;
     for (uint64_t c = 0; c < n_chunks; ++c) {
       ts.first = first + c * kChunk;
       ts.count = (c + 1 < n_chunks) ? kChunk : count - c * kChunk;
       ts.ev_mid = evs[3 * c + 1];
       cudaEventRecord(evs[3 * c], s);
-      if ((rc = run_transport(ts, s))) return fail(rc);
+      MCS_TRY(run_transport(ts, s));
       cudaEventRecord(evs[3 * c + 2], s);
       // remember the largest queue fill, empty the queue for the next chunk
       count_launch();
       queue_reset_kernel<<<1, 1, 0, s>>>(ctr.as<unsigned long long>());
-      if (cudaGetLastError() != cudaSuccess) { set_error("queue reset launch failed"); return fail(MC_ECUDA); }
+      if (cudaGetLastError() != cudaSuccess) { set_error("queue reset launch failed"); return MC_ECUDA; }
     }
-    if (cudaMemcpyAsync(hctr, ctr.p, sizeof(hctr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(hctr, ctr.p, kCounters * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("transport failed: %s", cudaGetErrorString(cudaGetLastError()));
-      return fail(MC_ECUDA);
+      return MC_ECUDA;
     }
     if (hctr[0] <= cap && hctr[6] <= cap_q) break;
     if (hctr[0] >= 0xFFFFFFFFull) {
       set_error("%llu events exceed the 2^32 limit of one build; split the history range", hctr[0]);
-      return fail(MC_EINVAL);
+      return MC_EINVAL;
     }
     // rerun with room for everything counted (a lost queue entry also lost
     // its detections, so the event count can grow once more)
@@ -437,31 +436,58 @@ static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
     if (hctr[0] > cap) cap = hctr[0] + hctr[0] / 8;
     if (attempt == 2) {
       set_error("transport buffers kept overflowing");
-      return fail(MC_ECUDA);
+      return MC_ECUDA;
     }
   }
-  float t_tr = 0.f, t_det = 0.f;
   for (uint64_t c = 0; c < n_chunks; ++c) {
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, evs[3 * c], evs[3 * c + 1]);
     cudaEventElapsedTime(&b, evs[3 * c + 1], evs[3 * c + 2]);
-    t_tr += a;
-    t_det += b;
+    out.ms_transport += a;
+    out.ms_detect += b;
   }
-  cudaEventRecord(evs[0], s);  // reused as the assembly start
-  esc.release();
-  sys->n_events = (int64_t)hctr[0];
-  for (int f = 0; f < 4; ++f) sys->fates[f] = hctr[1 + f];
-  rc = assemble_system(sys, events, sys->n_events, s, weighted ? weights.as<uint64_t>() : nullptr);
+  return MC_OK;
+}
+
+static int build_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
+                           mc_system **out) {
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete sys; return rc; };
+  const TransportSetup &ts = pl->ts;
+  sys->n_rows = (int64_t)ts.n_views * ts.bins_u * ts.bins_v;
+  sys->n_cols = (int64_t)ts.nx * ts.ny * ts.nz;
+  sys->first = first;
+  sys->count = count;
+  const bool weighted = ts.forced != 0 || ts.forced_dir != 0;
+  Tally t;
+  int rc = tally_from_plan(pl, first, count, seed, s, t);
   if (rc) return fail(rc);
-  weights.release();
-  if ((rc = finish_system(sys, s))) return fail(rc);
-  cudaEventRecord(e_end, s);
-  cudaEventSynchronize(e_end);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    set_error("cudaEventCreate failed");
+    return fail(MC_ECUDA);
+  }
+  cudaEventRecord(e0, s);
+  sys->n_events = (int64_t)t.hctr[0];
+  for (int f = 0; f < 4; ++f) sys->fates[f] = t.hctr[1 + f];
+  rc = assemble_system(sys, t.events, sys->n_events, s, weighted ? t.weights.as<uint64_t>() : nullptr);
+  if (rc == MC_OK) {
+    t.weights.release();
+    rc = finish_system(sys, s);
+  }
   float t_asm = 0.f;
-  cudaEventElapsedTime(&t_asm, evs[0], e_end);
-  sys->ms_transport = t_tr;
-  sys->ms_detect = t_det;
+  if (rc == MC_OK) {
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&t_asm, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return fail(rc);
+  sys->ms_transport = t.ms_transport;
+  sys->ms_detect = t.ms_detect;
   sys->ms_assembly = t_asm;
   *out = sys;
   return MC_OK;
@@ -471,6 +497,72 @@ __global__ void events_to_keys_kernel(const int32_t *rows, const int32_t *cols, 
                                       unsigned long long *keys) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     keys[i] = (unsigned long long)cols[i] * m + (unsigned long long)rows[i];
+}
+
+// ---------------------------------------------------------------------------
+// routing tally events to the parts that own their views (multi-GPU split)
+// ---------------------------------------------------------------------------
+constexpr int kMaxParts = 1024;
+constexpr int kRouteThreads = 256;
+
+// Part of event key v M + j: part_of_view[j / rows_per_view].
+__device__ __forceinline__ int route_part(uint64_t key, uint64_t m, uint64_t rpv, const int32_t *part_of_view) {
+  return part_of_view[(key % m) / rpv];
+}
+
+__global__ void route_count_kernel(const uint64_t *keys, int64_t n, uint64_t m, uint64_t rpv,
+                                   const int32_t *part_of_view, int n_parts, unsigned long long *counts) {
+  __shared__ unsigned int s_cnt[kMaxParts];
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x) s_cnt[p] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&s_cnt[route_part(keys[i], m, rpv, part_of_view)], 1u);
+  __syncthreads();
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x)
+    if (s_cnt[p]) atomicAdd(&counts[p], (unsigned long long)s_cnt[p]);
+}
+
+// Each block handles one contiguous chunk of the keys: counts its events per
+// part, reserves a range per part from the global cursors, then writes each
+// event, renumbered to its part's rows (key' = v M_p + j - row0_p), into the
+// part's range.  The order inside a part is not fixed; assembly sorts.
+__global__ void route_scatter_kernel(const uint64_t *keys, int64_t n, uint64_t m, uint64_t rpv,
+                                     const int32_t *part_of_view, const uint64_t *row0, const uint64_t *m_part,
+                                     int n_parts, int64_t chunk, unsigned long long *cursor, uint64_t *out) {
+  __shared__ unsigned int s_cnt[kMaxParts];
+  __shared__ unsigned long long s_base[kMaxParts];
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x) s_cnt[p] = 0u;
+  __syncthreads();
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+    atomicAdd(&s_cnt[route_part(keys[i], m, rpv, part_of_view)], 1u);
+  __syncthreads();
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x) {
+    s_base[p] = s_cnt[p] ? atomicAdd(&cursor[p], (unsigned long long)s_cnt[p]) : 0ull;
+    s_cnt[p] = 0u;
+  }
+  __syncthreads();
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const uint64_t k = keys[i];
+    const uint64_t j = k % m, v = k / m;
+    const int p = part_of_view[j / rpv];
+    const unsigned int o = atomicAdd(&s_cnt[p], 1u);
+    out[s_base[p] + o] = v * m_part[p] + (j - row0[p]);
+  }
+}
+
+// largest key of a list (validation of keys handed in by the caller)
+__global__ void max_key_kernel(const uint64_t *keys, int64_t n, unsigned long long *mx) {
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = keys[i] > m ? keys[i] : m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
 }
 
 }  // namespace mcs
@@ -497,6 +589,142 @@ int mc_plan_build(mc_plan *plan, uint64_t first, uint64_t count, uint64_t seed, 
   if (!plan || !out) { set_error("NULL argument"); return MC_EINVAL; }
   *out = nullptr;
   return build_from_plan(plan, first, count, seed, API_STREAM(stream), out);
+}
+
+int mc_plan_tally(mc_plan *plan, uint64_t first, uint64_t count, uint64_t seed, uint64_t *keys_dev, int64_t capacity,
+                  int64_t *n_events_out, uint64_t *fates_host, void *stream) {
+  clear_error();
+  if (!plan || !n_events_out) { set_error("NULL argument"); return MC_EINVAL; }
+  if (plan->ts.forced || plan->ts.forced_dir) {
+    set_error("mc_plan_tally: weighted (forced-detection / forced-direction) plans have no plain event list");
+    return MC_EINVAL;
+  }
+  if (capacity < 0 || (capacity > 0 && !keys_dev)) { set_error("bad key buffer"); return MC_EINVAL; }
+  cudaStream_t s = API_STREAM(stream);
+  Tally t;
+  MCS_TRY(tally_from_plan(plan, first, count, seed, s, t));
+  const int64_t n = (int64_t)t.hctr[0];
+  *n_events_out = n;
+  if (fates_host)
+    for (int f = 0; f < 4; ++f) fates_host[f] = t.hctr[1 + f];
+  if (n > capacity) {
+    set_error("mc_plan_tally: %lld events do not fit the buffer of %lld keys (the count is in *n_events_out; the "
+              "tally is deterministic, repeat with a larger buffer)",
+              (long long)n, (long long)capacity);
+    return MC_EINVAL;
+  }
+  if (n > 0) MCS_CUDA(cudaMemcpyAsync(keys_dev, t.events.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
+int mc_events_route(const uint64_t *keys_dev, int64_t n_events, int64_t n_rows, int64_t rows_per_view, int32_t n_parts,
+                    uint64_t *out_dev, int64_t *part_counts_host, void *stream) {
+  clear_error();
+  if (!part_counts_host || (n_events > 0 && (!keys_dev || !out_dev))) { set_error("NULL argument"); return MC_EINVAL; }
+  if (n_events < 0 || n_rows < 1 || rows_per_view < 1 || n_rows % rows_per_view != 0) {
+    set_error("sizes out of range: n_rows must be a positive multiple of rows_per_view");
+    return MC_EINVAL;
+  }
+  const int64_t n_views = n_rows / rows_per_view;
+  if (n_parts < 1 || n_parts > kMaxParts || n_parts > n_views) {
+    set_error("n_parts must be in 1 .. min(views, %d)", kMaxParts);
+    return MC_EINVAL;
+  }
+  std::vector<int32_t> pov((size_t)n_views);
+  std::vector<uint64_t> row0((size_t)n_parts), m_part((size_t)n_parts);
+  for (int p = 0; p < n_parts; ++p) {
+    const int64_t v0 = (int64_t)p * n_views / n_parts, v1 = (int64_t)(p + 1) * n_views / n_parts;
+    for (int64_t k = v0; k < v1; ++k) pov[(size_t)k] = p;
+    row0[(size_t)p] = (uint64_t)(v0 * rows_per_view);
+    m_part[(size_t)p] = (uint64_t)((v1 - v0) * rows_per_view);
+  }
+  cudaStream_t s = API_STREAM(stream);
+  DevBuf d_pov, d_row0, d_m, d_cnt;
+  MCS_TRY(d_pov.alloc(pov.size() * 4, s));
+  MCS_TRY(d_row0.alloc((size_t)n_parts * 8, s));
+  MCS_TRY(d_m.alloc((size_t)n_parts * 8, s));
+  MCS_TRY(d_cnt.alloc((size_t)n_parts * 8 * 2, s));
+  MCS_CUDA(cudaMemcpyAsync(d_pov.p, pov.data(), pov.size() * 4, cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(d_row0.p, row0.data(), (size_t)n_parts * 8, cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemcpyAsync(d_m.p, m_part.data(), (size_t)n_parts * 8, cudaMemcpyHostToDevice, s));
+  MCS_CUDA(cudaMemsetAsync(d_cnt.p, 0, (size_t)n_parts * 8 * 2, s));
+  unsigned long long *cnt = d_cnt.as<unsigned long long>(), *cursor = cnt + n_parts;
+  std::vector<unsigned long long> h((size_t)n_parts, 0ull);
+  if (n_events > 0) {
+    int g = (int)((n_events + kRouteThreads - 1) / kRouteThreads);
+    if (g > device_sm_count() * 8) g = device_sm_count() * 8;
+    count_launch();
+    route_count_kernel<<<g, kRouteThreads, 0, s>>>(keys_dev, n_events, (uint64_t)n_rows, (uint64_t)rows_per_view,
+                                                   d_pov.as<int32_t>(), n_parts, cnt);
+    MCS_LAUNCHED();
+    MCS_CUDA(cudaMemcpyAsync(h.data(), cnt, (size_t)n_parts * 8, cudaMemcpyDeviceToHost, s));
+    MCS_CUDA(cudaStreamSynchronize(s));
+    std::vector<unsigned long long> start((size_t)n_parts, 0ull);
+    for (int p = 1; p < n_parts; ++p) start[(size_t)p] = start[(size_t)p - 1] + h[(size_t)p - 1];
+    MCS_CUDA(cudaMemcpyAsync(cursor, start.data(), (size_t)n_parts * 8, cudaMemcpyHostToDevice, s));
+    const int64_t chunk = 8192;
+    const int64_t nb = (n_events + chunk - 1) / chunk;
+    count_launch();
+    route_scatter_kernel<<<(unsigned)nb, kRouteThreads, 0, s>>>(keys_dev, n_events, (uint64_t)n_rows,
+                                                                (uint64_t)rows_per_view, d_pov.as<int32_t>(),
+                                                                d_row0.as<uint64_t>(), d_m.as<uint64_t>(), n_parts,
+                                                                chunk, cursor, out_dev);
+    MCS_LAUNCHED();
+  }
+  MCS_CUDA(cudaStreamSynchronize(s));
+  for (int p = 0; p < n_parts; ++p) part_counts_host[p] = (int64_t)h[(size_t)p];
+  return MC_OK;
+}
+
+int mc_system_from_keys(int64_t n_rows, int64_t n_cols, const uint64_t *keys_dev, int64_t n_keys, uint64_t first,
+                        uint64_t count, void *stream, mc_system **out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return MC_EINVAL; }
+  *out = nullptr;
+  if (n_rows < 1 || n_cols < 1 || n_rows >= (1ll << 31) || n_cols >= (1ll << 31) || n_keys < 0 ||
+      n_keys >= 0xFFFFFFFFll) {
+    set_error("sizes out of range");
+    return MC_EINVAL;
+  }
+  if (n_keys > 0 && !keys_dev) { set_error("keys_dev is NULL"); return MC_EINVAL; }
+  cudaStream_t s = API_STREAM(stream);
+  mc_system *sys = new (std::nothrow) mc_system();
+  if (!sys) { set_error("out of host memory"); return MC_ENOMEM; }
+  auto fail = [&](int rc) { delete sys; return rc; };
+  sys->n_rows = n_rows;
+  sys->n_cols = n_cols;
+  sys->first = first;
+  sys->count = count;
+  sys->n_events = n_keys;
+  DevBuf keys, mx;
+  int rc;
+  if ((rc = keys.alloc((size_t)(n_keys > 0 ? n_keys : 1) * 8, s)) || (rc = mx.alloc(8, s))) return fail(rc);
+  if (n_keys > 0) {
+    if (cudaMemcpyAsync(keys.p, keys_dev, (size_t)n_keys * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(mx.p, 0, 8, s) != cudaSuccess) {
+      set_error("key copy failed");
+      return fail(MC_ECUDA);
+    }
+    int g = (int)((n_keys + 255) / 256);
+    if (g > device_sm_count() * 8) g = device_sm_count() * 8;
+    count_launch();
+    max_key_kernel<<<g, 256, 0, s>>>(keys.as<uint64_t>(), n_keys, mx.as<unsigned long long>());
+    unsigned long long hmx = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&hmx, mx.p, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("key check failed");
+      return fail(MC_ECUDA);
+    }
+    if (hmx >= (unsigned long long)n_rows * (unsigned long long)n_cols) {
+      set_error("key %llu is out of range for %lld rows x %lld columns", hmx, (long long)n_rows, (long long)n_cols);
+      return fail(MC_EINVAL);
+    }
+  }
+  if ((rc = assemble_system(sys, keys, n_keys, s))) return fail(rc);
+  if ((rc = finish_system(sys, s))) return fail(rc);
+  *out = sys;
+  return MC_OK;
 }
 
 int mc_plan_free(mc_plan *plan) {
@@ -885,6 +1113,18 @@ int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const float *bp
   if (!sens_dev || !bp_dev || !x_dev || n < 0) { set_error("NULL argument or negative size"); return MC_EINVAL; }
   if (!(alpha > 0.0) || !std::isfinite(alpha)) { set_error("alpha must be positive"); return MC_EINVAL; }
   return pgd_step(n, alpha, sens_dev, bp_dev, gp_dev, x_dev, API_STREAM(stream));
+}
+
+int mc_vector_sum(int64_t n, const float *v_dev, double *out_dev, void *stream) {
+  clear_error();
+  if (n < 0 || !out_dev || (n > 0 && !v_dev)) { set_error("bad argument"); return MC_EINVAL; }
+  return vector_sum(n, v_dev, out_dev, API_STREAM(stream));
+}
+
+int mc_mlem_start(int64_t n, const double *sens_dev, double sum_y, float *x_dev, void *stream) {
+  clear_error();
+  if (n < 0 || (n > 0 && (!sens_dev || !x_dev))) { set_error("bad argument"); return MC_EINVAL; }
+  return mlem_start(n, sens_dev, sum_y, x_dev, API_STREAM(stream));
 }
 
 int mc_system_set_spmv_layout(mc_system *sys, int32_t fwd, int32_t bwd, void *stream) {

@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
     } else {
       out[gid] = ratio_out<MODE>(acc, gid, y, rmap, add);
       if (LL) {
+        // a bin with an empty row is left out of the y ln q sum (q = 0 for
+        // every image: the term carries no information about x)
         const float yj = y[gid];
-        ll = (yj > 0.0f ? (double)yj * log((double)acc) : 0.0) - (double)acc;
+        ll = (yj > 0.0f && e > b ? (double)yj * log((double)acc) : 0.0) - (double)acc;
       }
     }
   }
@@ -300,7 +302,8 @@ __device__ __forceinline__ float stream_segment(const float *s_prod, uint32_t b,
 }
 
 // Reduces every segment j in [j0, j1) of the tile from shared memory and
-// hands its sum to out.store(j, acc, out.load(j)).  Warp mode: one warp per
+// hands its sum to out.store(j, acc, out.load(j), segment j non-empty).  Warp
+// mode: one warp per
 // segment.  Thread mode: each thread takes kSegBatch segments kStreamThreads
 // apart and issues their pointer loads and out.load() before any reduction,
 // so that short segments do not leave one load in flight per thread.
@@ -324,7 +327,7 @@ __device__ __forceinline__ void stream_segments_thread(const uint32_t *__restric
 #pragma unroll
     for (int u = 0; u < kSegBatch; ++u) {
       const uint32_t j = base + u * kStreamThreads;
-      if (j < j1) out.store(j, stream_segment<false>(s_prod, b[u] - p0, e[u] - p0), pre[u]);
+      if (j < j1) out.store(j, stream_segment<false>(s_prod, b[u] - p0, e[u] - p0), pre[u], e[u] > b[u]);
     }
   }
 }
@@ -334,8 +337,9 @@ __device__ __forceinline__ void stream_segments(const uint32_t *__restrict__ ptr
                                                 uint32_t p0, const float *s_prod, Out &out) {
   if (WARP) {
     for (uint32_t j = j0 + (threadIdx.x >> 5); j < j1; j += kStreamThreads / 32) {
-      const float acc = stream_segment<true>(s_prod, ptr[j] - p0, ptr[j + 1] - p0);
-      if ((threadIdx.x & 31) == 0) out.store(j, acc, out.load(j));
+      const uint32_t b = ptr[j], e = ptr[j + 1];
+      const float acc = stream_segment<true>(s_prod, b - p0, e - p0);
+      if ((threadIdx.x & 31) == 0) out.store(j, acc, out.load(j), e > b);
     }
   } else {
     stream_segments_thread(ptr, j0, j1, p0, s_prod, out);
@@ -353,12 +357,14 @@ struct FwdOut {
   const float *__restrict__ add;
   double ll;
   __device__ __forceinline__ float load(uint32_t r) const { return (MODE == 1) ? y[r] : 0.0f; }
-  __device__ __forceinline__ void store(uint32_t r, float acc, float yv) {
+  // `reached`: the row holds an entry (a bin with an empty row is left out
+  // of the y ln q sum)
+  __device__ __forceinline__ void store(uint32_t r, float acc, float yv, bool reached) {
     if (MODE == 0) {
       out[r] = acc;
     } else if (MODE == 1) {
       out[r] = acc > 0.0f ? yv / acc : 0.0f;
-      if (LL) ll += (yv > 0.0f ? (double)yv * log((double)acc) : 0.0) - (double)acc;
+      if (LL) ll += (yv > 0.0f && reached ? (double)yv * log((double)acc) : 0.0) - (double)acc;
     } else {
       out[r] = ratio_out<MODE>(acc, r, y, rmap, add);
     }
@@ -382,7 +388,7 @@ struct BackOut {
     p.x = MODE == 0 ? 0.0f : x[v];
     return p;
   }
-  __device__ __forceinline__ void store(uint32_t v, float acc, const BackPre &p) const {
+  __device__ __forceinline__ void store(uint32_t v, float acc, const BackPre &p, bool) const {
     if (MODE == 0) {
       x[v] = acc * p.inv_n;
     } else {
@@ -693,6 +699,55 @@ int sensitivity(const mc_system *sys, double *out, cudaStream_t s) {
     const uint32_t *nv = nullptr;
     const double *cs = proj_sens_terms(sys, &nv);
     count_launch(); sensitivity_kernel<<<grid_stride_blocks(sys->n_cols), 256, 0, s>>>(cs, nv, sys->n_cols, out);
+  }
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+// FP64 sum of n floats (or doubles) in a fixed order: block partials over a
+// fixed grid, then one block
+template <typename T>
+__global__ void partial_sums_kernel(const T *v, int64_t n, double *part) {
+  __shared__ double s_tmp[32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)v[i];
+  const double t = block_sum_double(acc, s_tmp);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+int vector_sum(int64_t n, const float *v, double *out, cudaStream_t s) {
+  const int nb = 256;
+  DevBuf part;
+  MCS_TRY(part.alloc(nb * sizeof(double), s));
+  count_launch();
+  partial_sums_kernel<float><<<nb, 256, 0, s>>>(v, n, part.as<double>());
+  count_launch();
+  sum_partials_kernel<<<1, 1024, 0, s>>>(part.as<double>(), nb, out);
+  MCS_LAUNCHED();
+  return MC_OK;
+}
+
+// x_v = sum_y / (sum of sens) where sens_v > 0, else 0 (the uniform start
+// image of ML-EM from a sensitivity summed over several systems)
+__global__ void start_fill_kernel(const double *total, double sum_y, const double *sens, int64_t n, float *x) {
+  const double ts = *total;
+  const float x0 = ts > 0.0 ? (float)(sum_y / ts) : 0.0f;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = sens[v] > 0.0 ? x0 : 0.0f;
+}
+
+int mlem_start(int64_t n, const double *sens, double sum_y, float *x, cudaStream_t s) {
+  const int nb = 256;
+  DevBuf part;
+  MCS_TRY(part.alloc((nb + 1) * sizeof(double), s));
+  count_launch();
+  partial_sums_kernel<double><<<nb, 256, 0, s>>>(sens, n, part.as<double>());
+  count_launch();
+  sum_partials_kernel<<<1, 1024, 0, s>>>(part.as<double>(), nb, part.as<double>() + nb);
+  if (n > 0) {
+    count_launch();
+    start_fill_kernel<<<grid_stride_blocks(n), 256, 0, s>>>(part.as<double>() + nb, sum_y, sens, n, x);
   }
   MCS_LAUNCHED();
   return MC_OK;
@@ -1067,7 +1122,7 @@ struct BatchFwdOut {
   const float *__restrict__ y;
   float *__restrict__ r;
   __device__ __forceinline__ float load(uint32_t j) const { return y[j]; }
-  __device__ __forceinline__ void store(uint32_t j, float acc, float yv) const { r[j] = acc > 0.0f ? yv / acc : 0.0f; }
+  __device__ __forceinline__ void store(uint32_t j, float acc, float yv, bool) const { r[j] = acc > 0.0f ? yv / acc : 0.0f; }
 };
 
 __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,

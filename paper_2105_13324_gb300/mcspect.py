@@ -31,7 +31,8 @@ FATE_NAMES = ("absorbed", "below_window", "escape", "cap")
 
 # every symbol include/mcspect.h declares
 EXPORTED = (
-    "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_build_system", "mc_build_system_range", "mc_system_from_events",
+    "mc_plan_create", "mc_plan_build", "mc_plan_free", "mc_plan_tally", "mc_events_route", "mc_system_from_keys",
+    "mc_vector_sum", "mc_mlem_start", "mc_build_system", "mc_build_system_range", "mc_system_from_events",
     "mc_system_from_weighted_events", "mc_system_export_values", "mc_system_free",
     "mc_system_info_get", "mc_system_export_csc", "mc_system_export_csr", "mc_system_set_value_type", "mc_system_set_spmv_layout",
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
@@ -101,6 +102,11 @@ def load(path: str | None = None):
             "mc_plan_create": [vp, vp, vp, vp],
             "mc_plan_build": [vp, u64, u64, u64, vp, vp],
             "mc_plan_free": [vp],
+            "mc_plan_tally": [vp, u64, u64, u64, vp, i64, vp, vp, vp],
+            "mc_events_route": [vp, i64, i64, i64, i32, vp, vp, vp],
+            "mc_system_from_keys": [i64, i64, vp, i64, u64, u64, vp, vp],
+            "mc_vector_sum": [i64, vp, vp, vp],
+            "mc_mlem_start": [i64, vp, dbl, vp, vp],
             "mc_build_system": [vp, vp, u64, u64, vp, vp],
             "mc_build_system_range": [vp, vp, u64, u64, u64, vp, vp],
             "mc_system_from_events": [i64, i64, vp, vp, i64, u64, u64, vp, vp],
@@ -315,6 +321,64 @@ def mc_plan_build(plan: Plan, first: int, count: int, seed: int, stream=None) ->
 
 def mc_plan_free(plan: Plan):
     plan.free()
+
+
+def mc_plan_tally(plan: Plan, first: int, count: int, seed: int, stream=None):
+    """Event keys v*M + j (int64 CUDA tensor holding the unsigned keys) and
+    fates of histories first..first+count-1; the buffer is resized and the
+    deterministic tally repeated if the first estimate is too small."""
+    import torch
+    if not plan._h:
+        raise ValueError("plan was freed")
+    n = ctypes.c_int64(0)
+    fates = (ctypes.c_uint64 * 4)()
+    cap = max(1024, int(count) // 64)
+    for _ in range(2):
+        keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+        rc = load().mc_plan_tally(plan._h, int(first), int(count), int(seed), _dev_ptr(keys), cap, ctypes.byref(n),
+                                  fates, _stream_ptr(stream))
+        if rc == MC_OK:
+            return keys[:n.value], [int(f) for f in fates]
+        if n.value <= cap:
+            _check(rc)
+        cap = int(n.value)
+    _check(rc)
+
+
+def mc_events_route(keys, n_rows: int, rows_per_view: int, n_parts: int, stream=None):
+    """Events grouped by the part owning their view, rows renumbered per
+    part: (int64 CUDA tensor, list of per-part counts)."""
+    import torch
+    out = torch.empty_like(keys)
+    counts = (ctypes.c_int64 * int(n_parts))()
+    n = int(keys.numel())
+    _check(load().mc_events_route(_dev_ptr(keys, torch.int64) if n else None, n, int(n_rows), int(rows_per_view),
+                                  int(n_parts), _dev_ptr(out, torch.int64) if n else None, counts,
+                                  _stream_ptr(stream)))
+    return out, [int(c) for c in counts]
+
+
+def mc_system_from_keys(n_rows: int, n_cols: int, keys, first: int, count: int, stream=None) -> System:
+    import torch
+    n = int(keys.numel())
+    h = ctypes.c_void_p()
+    _check(load().mc_system_from_keys(int(n_rows), int(n_cols), _dev_ptr(keys, torch.int64) if n else None, n,
+                                      int(first), int(count), _stream_ptr(stream), ctypes.byref(h)))
+    return System(h)
+
+
+def mc_vector_sum(v, out, stream=None):
+    import torch
+    _check(load().mc_vector_sum(int(v.numel()), _dev_ptr(v, torch.float32), _dev_ptr(out, torch.float64),
+                                _stream_ptr(stream)))
+    return out
+
+
+def mc_mlem_start(sens, sum_y: float, x, stream=None):
+    import torch
+    _check(load().mc_mlem_start(int(x.numel()), _dev_ptr(sens, torch.float64), float(sum_y),
+                                _dev_ptr(x, torch.float32), _stream_ptr(stream)))
+    return x
 
 
 def mc_kernel_launches() -> int:

@@ -392,3 +392,27 @@ def test_half_and_float_values_give_identical_images():
         out[vt] = (x.cpu().numpy(), np.asarray(ll), b.cpu().numpy())
     for a, b in zip(out["f32"], out["f16"]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("layout", [0, 4])
+def test_loglik_leaves_out_bins_with_an_empty_row(mc, layout):
+    # rows 1 and 3 are empty but carry counts (as data from an independent
+    # MC realisation does): the likelihood is finite and equals the oracle's
+    import torch
+    rows = np.array([0, 0, 2, 2, 2, 4], np.int32)
+    cols = np.array([0, 1, 1, 2, 2, 0], np.int32)
+    s = mc.mc_system_from_events(5, 3, rows, cols, 0, 6)
+    mc.mc_system_set_spmv_layout(s, layout, layout)
+    c = oracle.system_counts(rows, cols, 5, 3)
+    a = oracle.system_matrix(c, oracle.histories_per_voxel(3, 0, 6))
+    y = np.array([3.0, 2.0, 5.0, 7.0, 1.0], np.float32)
+    x = np.array([1.5, 0.5, 2.0], np.float32)
+    v = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mc.mc_loglik(s, _dev(x), _dev(y), v)
+    want = oracle.loglik(a, x.astype(np.float64), y.astype(np.float64))
+    assert np.isfinite(want)
+    assert float(v.item()) == pytest.approx(want, rel=1e-6)
+    ll = mc.mlem_iterate(s, _dev(y), _dev(x), 4, loglik=True)
+    _, llo = oracle.mlem(a, y.astype(np.float64), x.astype(np.float64), 4, with_loglik=True)
+    np.testing.assert_allclose(ll, llo, rtol=1e-6)
+    s.free()

@@ -115,3 +115,21 @@ def test_toy_4cubed_reaches_the_ml_optimum():
     assert np.max(np.abs(g[on]) / s[on]) < 1e-4
     assert np.max(g[~on] / s[~on]) < 1e-3
     np.testing.assert_allclose(x_em[on], res.x[on], rtol=2e-3, atol=2e-3)
+
+
+def test_loglik_leaves_out_bins_the_model_cannot_reach():
+    # row 2 of A is empty: q_2 = 0 for every image, so its y ln q term is
+    # left out (by hand: L = 3 ln 2 + 1 ln 3 - (2 + 3)); ML-EM ignores the
+    # bin (r_2 = 0) and increases this L monotonically
+    a = sp.csr_matrix(np.array([[1.0, 1.0], [0.0, 3.0], [0.0, 0.0]]))
+    y = np.array([3.0, 1.0, 4.0])
+    x = np.array([1.0, 1.0])
+    assert oracle.loglik(a, x, y) == pytest.approx(3 * np.log(2.0) + np.log(3.0) - 5.0, rel=1e-15)
+    x = oracle.mlem_init(a, y)
+    ll = [oracle.loglik(a, x, y)]
+    for _ in range(20):
+        x = oracle.mlem_step(a, y, x)
+        ll.append(oracle.loglik(a, x, y))
+    assert np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -1e-12 * np.abs(ll[1:]))
+    # a reachable bin with q_j = 0 and y_j > 0 still gives -inf
+    assert oracle.loglik(a, np.array([0.0, 0.0]), y) == -np.inf
