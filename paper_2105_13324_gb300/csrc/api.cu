@@ -301,11 +301,15 @@ static int run_transport(const TransportSetup &ts, cudaStream_t s) {
   return ts.precision == MC_FP64 ? launch_transport_f64(ts, s) : launch_transport_f32(ts, s);
 }
 
-// Lanes per row (column) of the row-group kernels: about 8 entries per lane
-// (two 4-entry vector steps), at most a warp.
+// Lanes per row (column) of the row-group kernels from the mean length:
+// about 12 or more entries per lane, 16 lanes at most below 1024 entries
+// (measured on the 128^3 torso systems: rows of ~70 entries run best with 8
+// lanes, rows of ~350 with 16; 32 lanes leave too few loads in flight per
+// lane).
 static int pick_group(double mean_len) {
   int g = 1;
-  while (g < 32 && 8 * g < mean_len) g <<= 1;
+  while (g < 16 && 12 * g < mean_len) g <<= 1;
+  if (mean_len >= 1024.0) g = 32;
   return g;
 }
 
@@ -424,6 +428,15 @@ static int tally_from_plan(mc_plan *pl, uint64_t first, uint64_t count, uint64_t
         cudaStreamSynchronize(s) != cudaSuccess) {
       set_error("transport failed: %s", cudaGetErrorString(cudaGetLastError()));
       return MC_ECUDA;
+    }
+    {
+      // every history ends in exactly one fate; fewer means a transport
+      // launch gave up (its random-word producer stopped answering)
+      const unsigned long long done = hctr[1] + hctr[2] + hctr[3] + hctr[4];
+      if (done != count) {
+        set_error("transport finished %llu of %llu histories", done, (unsigned long long)count);
+        return MC_ECUDA;
+      }
     }
     if (hctr[0] <= cap && hctr[6] <= cap_q) break;
     if (hctr[0] >= 0xFFFFFFFFull) {
