@@ -60,6 +60,37 @@ TRANSPORT_DRAM_BYTES_PER_HISTORY = (16029184 + 987994624) / 1e9
 MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
 
 
+# Nominal issue rates per SM and clock of the pipes the transport kernel
+# uses: FP32/INT32 lanes, 32x32->64-bit integer multiplies (Philox; the
+# wide IMAD issues at half the FP32 rate) and the multi-function unit
+# (log, sin/cos, reciprocal, reciprocal square root).
+PIPE_RATES = {"fp32_int_lanes": 128, "imad_wide": 64, "mufu": 16}
+MUFU_PER_FLIGHT = 1.0      # log of the flight length
+MUFU_PER_SCATTER = 2.2 + 5.0  # a reciprocal per rejection trial (~2.2), sin+cos, two rsqrt, a reciprocal
+MUFU_PER_EMISSION = 3.0    # sin+cos of the azimuth, rsqrt
+IMAD_PER_BLOCK = 20.0      # Philox4x32-10: two wide multiplies per round
+
+
+def transport_per_pipe(rec, flights, sm_count, sm_mhz, histories_per_s, lane_ops):
+    """Per-pipe bounds of the transport kernel from the FP64 trace of a
+    history sample: operations per history on each pipe, the histories/s
+    that pipe alone would allow at its nominal rate, and the fraction of it
+    achieved.  Philox blocks are the words drawn rounded up to blocks (the
+    minimum any kernel must generate)."""
+    blocks = np.ceil(rec["n_draws"] / 4.0).mean()
+    per_hist = {"fp32_int_lanes": float(lane_ops),
+                "imad_wide": IMAD_PER_BLOCK * float(blocks),
+                "mufu": float((MUFU_PER_FLIGHT * flights + MUFU_PER_SCATTER * rec["n_compton"]).mean()
+                              + MUFU_PER_EMISSION)}
+    out = {}
+    for pipe, n in per_hist.items():
+        bound = sm_count * PIPE_RATES[pipe] * sm_mhz * 1e6 / n
+        out[pipe] = {"ops_per_history": n, "rate_per_sm_clock": PIPE_RATES[pipe], "bound_histories_per_s": bound,
+                     "frac": histories_per_s / bound}
+    out["philox_blocks_per_history"] = float(blocks)
+    return out
+
+
 def _launch_histories(g) -> int:
     """Histories per transport launch of an analog FP32 build: the library
     runs the longest power-of-two chunk in 2^27..2^30 whose escape queue
@@ -787,6 +818,7 @@ def run_ours(args, w):
     alu_peak = sm_count * ALU_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12  # T lane-ops/s
     t_tr = float(np.mean(t_transport))
     achieved = ops * H / (t_tr * 1e-3) / 1e12
+    per_pipe = transport_per_pipe(rec, flights, sm_count, sm_max_mhz, H / (t_tr * 1e-3), ops)
 
     # end to end through the public API with host buffers
     y_pin = torch.as_tensor(y_host).pin_memory()
@@ -852,6 +884,7 @@ def run_ours(args, w):
                                           "capture of one 1e9-history torso128 launch",
                          "kernel": "transport_kernel<float>",
                          "ops_per_history": ops,
+                         "per_pipe": per_pipe,
                          "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {sm_max_mhz:.0f} MHz"},
             "roofline_mlem": {"bound": "hbm", "achieved": mlem_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm_gbs,
                               "unit": "GB/s", "frac": mlem_bytes / (it_ms * 1e-3) / 1e9 / hbm_gbs,
