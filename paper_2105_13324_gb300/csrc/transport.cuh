@@ -156,6 +156,8 @@ struct KRng {
 // than k words are left, and is called before each group of draws, so blocks
 // are generated where most lanes need them and no word is generated past
 // the end of a history.  The stream position is 4 * blocks - words left.
+// The head starts at slot 0 with each history, so block b always lands in
+// slots 4 (b mod 4) .. 4 (b mod 4) + 3 (head + words left = 4 b mod 16).
 constexpr int kRing = 16;
 constexpr int kRingThreads = 256;
 template <typename T> struct TArgs;
@@ -164,16 +166,16 @@ struct Ring {
   uint32_t tid, head, avail, blk, h_lo, h_hi;
   __device__ __forceinline__ void start(uint64_t h) {
     h_lo = (uint32_t)h; h_hi = (uint32_t)(h >> 32);
-    blk = 0; avail = 0;
+    blk = 0; avail = 0; head = 0;
   }
   template <typename A> __device__ __forceinline__ void refill(const A &a) {
     uint32_t c0 = blk, c1 = 0u, c2 = h_lo, c3 = h_hi;
     philox_rounds(c0, c1, c2, c3, a.rk);
-    const uint32_t p = head + avail;
-    buf[p & (kRing - 1)][tid] = c0;
-    buf[(p + 1) & (kRing - 1)][tid] = c1;
-    buf[(p + 2) & (kRing - 1)][tid] = c2;
-    buf[(p + 3) & (kRing - 1)][tid] = c3;
+    uint32_t *w = &buf[(blk & 3u) << 2][tid];  // four rows from here
+    w[0] = c0;
+    w[kRingThreads] = c1;
+    w[2 * kRingThreads] = c2;
+    w[3 * kRingThreads] = c3;
     avail += 4;
     blk += 1;
   }
