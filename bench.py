@@ -368,6 +368,17 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     batch_ms = float(np.median(ms))
+    # the same reconstruction with all iterations in one persistent launch
+    batch.mlem_persistent(n_iter, stream)
+    torch.cuda.synchronize()
+    ms_p = []
+    for _ in range(5):
+        e0.record(stream)
+        batch.mlem_persistent(n_iter, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p.append(e0.elapsed_time(e1))
+    batch_persistent_ms = float(np.median(ms_p))
     # one request at a time through a batch of one (compacted system, one
     # CUDA graph per reconstruction); before the autotuner, which may
     # replace a system's streaming tiles by row groups
@@ -397,6 +408,8 @@ def serving_benchmark(mc, n_phantoms: int, histories: int, n_iter: int, stream):
     sizes = sorted({int(ph.shape[0]) for ph, _, _, _ in mix})
     out = {"phantoms": n_phantoms, "grids": sizes, "histories_per_phantom": histories, "mlem_iters": n_iter,
            "build_s": build_s, "batch_ms": batch_ms, "images_per_s": n_phantoms / (batch_ms * 1e-3),
+           "batch_persistent_ms": batch_persistent_ms,
+           "persistent_images_per_s": n_phantoms / (batch_persistent_ms * 1e-3),
            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
            "sequential_images_per_s": n_phantoms / (sum(lat) * 1e-3),
            "latency_graph_ms_p50": float(np.percentile(lat_g, 50)),

@@ -408,6 +408,13 @@ typedef struct mc_batch mc_batch;
 MC_API int mc_batch_create(mc_system *const *systems, int32_t n, const float *const *y_dev, float *const *x_dev,
                            mc_batch **out);
 MC_API int mc_batch_mlem(mc_batch *batch, int32_t n_iter, void *stream);
+/* The same reconstruction as mc_batch_mlem (equal images) with all n_iter
+ * iterations of all systems in one persistent cooperative launch: the
+ * blocks stay resident and meet at a grid-wide barrier between the forward
+ * and back-projection halves of every iteration (the start images and the
+ * write-back are four short launches around it).  Not captured in a graph.
+ * MC_ECUDA if the device cannot launch cooperatively. */
+MC_API int mc_batch_mlem_persistent(mc_batch *batch, int32_t n_iter, void *stream);
 MC_API int mc_batch_free(mc_batch *batch);
 
 /* ML-EM like mlem_iterate, for callers that must not allocate device

@@ -88,6 +88,7 @@ int prior_quadratic(int nx, int ny, int nz, double beta, const T *x, T *grad, do
 int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const float *gp, float *x, cudaStream_t s);
 int batch_create(mc_system *const *sys, int n, const float *const *y, float *const *x, mc_batch **out);
 int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s);
+int batch_mlem_persistent(mc_batch *b, int n_iter, cudaStream_t s);
 void batch_free(mc_batch *b);
 int autotune(mc_system *sys, cudaStream_t s, int *fwd_choice, int *bwd_choice);
 int vector_sum(int64_t n, const float *v, double *out, cudaStream_t s);
@@ -1165,6 +1166,12 @@ int mc_batch_mlem(mc_batch *batch, int32_t n_iter, void *stream) {
   clear_error();
   if (!batch || n_iter < 0) { set_error("NULL batch or negative n_iter"); return MC_EINVAL; }
   return batch_mlem(batch, n_iter, API_STREAM(stream));
+}
+
+int mc_batch_mlem_persistent(mc_batch *batch, int32_t n_iter, void *stream) {
+  clear_error();
+  if (!batch || n_iter < 0) { set_error("NULL batch or negative n_iter"); return MC_EINVAL; }
+  return batch_mlem_persistent(batch, n_iter, API_STREAM(stream));
 }
 
 int mc_batch_free(mc_batch *batch) {

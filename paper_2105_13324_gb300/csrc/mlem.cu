@@ -11,6 +11,7 @@
 // CSR and CSC, so no floating-point atomics are used and the result is the
 // same from run to run.  Each row (column) is reduced by a group of G lanes,
 // G a power of two matched to the mean row (column) length.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -1104,13 +1105,14 @@ __device__ __forceinline__ int batch_find(const uint64_t *off, int n, uint64_t i
   return lo;
 }
 
-// The block's system descriptor is copied to shared memory once, so that
-// stores through its output pointers cannot force reloads of the others.
+// The block's system descriptor for global tile t is copied to shared
+// memory once, so that stores through its output pointers cannot force
+// reloads of the others.
 __device__ __forceinline__ const BatchSys &batch_desc(const BatchSys *systems, const uint64_t *off, int n_sys,
-                                                      BatchSys *s_desc, uint32_t &tile) {
-  const int k = batch_find(off, n_sys, blockIdx.x);
+                                                      BatchSys *s_desc, uint64_t t, uint32_t &tile) {
+  const int k = batch_find(off, n_sys, t);
   if (threadIdx.x == 0) *s_desc = systems[k];
-  tile = (uint32_t)(blockIdx.x - off[k]);
+  tile = (uint32_t)(t - off[k]);
   __syncthreads();
   return *s_desc;
 }
@@ -1125,13 +1127,13 @@ struct BatchFwdOut {
   __device__ __forceinline__ void store(uint32_t j, float acc, float yv, bool) const { r[j] = acc > 0.0f ? yv / acc : 0.0f; }
 };
 
-__global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
-                                                                    const uint64_t *__restrict__ tile_off,
-                                                                    int n_sys) {
-  __shared__ float s_prod[kStreamTile];
-  __shared__ BatchSys s_desc;
+// One forward (ratio) tile and one back-projection (EM update) tile of the
+// batch, by global tile index t
+__device__ __forceinline__ void batch_forward_tile(const BatchSys *__restrict__ systems,
+                                                   const uint64_t *__restrict__ tile_off, int n_sys, uint64_t t,
+                                                   float *s_prod, BatchSys *s_desc) {
   uint32_t tile;
-  const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
+  const BatchSys &S = batch_desc(systems, tile_off, n_sys, s_desc, t, tile);
   const uint32_t *__restrict__ ptr = S.row_ptr;
   const uint32_t j0 = S.csr_tiles[tile], j1 = S.csr_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
@@ -1142,12 +1144,11 @@ __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const Bat
   else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
 }
 
-__global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchSys *__restrict__ systems,
-                                                                 const uint64_t *__restrict__ tile_off, int n_sys) {
-  __shared__ float s_prod[kStreamTile];
-  __shared__ BatchSys s_desc;
+__device__ __forceinline__ void batch_back_tile(const BatchSys *__restrict__ systems,
+                                                const uint64_t *__restrict__ tile_off, int n_sys, uint64_t t,
+                                                float *s_prod, BatchSys *s_desc) {
   uint32_t tile;
-  const BatchSys &S = batch_desc(systems, tile_off, n_sys, &s_desc, tile);
+  const BatchSys &S = batch_desc(systems, tile_off, n_sys, s_desc, t, tile);
   const uint32_t *__restrict__ ptr = S.col_ptr;
   const uint32_t j0 = S.csc_tiles[tile], j1 = S.csc_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
@@ -1156,6 +1157,48 @@ __global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchS
   BackOut<1> o{S.invn_c, S.ics_c, S.x_c, S.xs_c};
   if (S.warp_bwd) stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
   else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
+}
+
+__global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
+                                                                    const uint64_t *__restrict__ tile_off,
+                                                                    int n_sys) {
+  __shared__ float s_prod[kStreamTile];
+  __shared__ BatchSys s_desc;
+  batch_forward_tile(systems, tile_off, n_sys, blockIdx.x, s_prod, &s_desc);
+}
+
+__global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchSys *__restrict__ systems,
+                                                                 const uint64_t *__restrict__ tile_off, int n_sys) {
+  __shared__ float s_prod[kStreamTile];
+  __shared__ BatchSys s_desc;
+  batch_back_tile(systems, tile_off, n_sys, blockIdx.x, s_prod, &s_desc);
+}
+
+// All n_iter iterations of every system in one cooperative launch: the
+// blocks stay resident, take the forward tiles in a grid-stride loop, meet
+// at a grid-wide barrier, take the back-projection tiles, and meet again
+// (the barrier the separate launches give).  Launched only through
+// cudaLaunchCooperativeKernel with every block resident.
+__global__ void __launch_bounds__(kStreamThreads) batch_persistent_kernel(const BatchSys *__restrict__ systems,
+                                                                       const uint64_t *__restrict__ tile_fwd,
+                                                                       uint64_t n_fwd,
+                                                                       const uint64_t *__restrict__ tile_bwd,
+                                                                       uint64_t n_bwd, int n_sys, int n_iter) {
+  __shared__ float s_prod[kStreamTile];
+  __shared__ BatchSys s_desc;
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  for (int it = 0; it < n_iter; ++it) {
+    for (uint64_t t = blockIdx.x; t < n_fwd; t += gridDim.x) {
+      batch_forward_tile(systems, tile_fwd, n_sys, t, s_prod, &s_desc);
+      __syncthreads();  // s_prod and s_desc are reused by the next tile
+    }
+    grid.sync();
+    for (uint64_t t = blockIdx.x; t < n_bwd; t += gridDim.x) {
+      batch_back_tile(systems, tile_bwd, n_sys, t, s_prod, &s_desc);
+      __syncthreads();
+    }
+    grid.sync();
+  }
 }
 
 // Non-empty segments of a pointer array: flags (1 per non-empty segment,
@@ -1469,6 +1512,45 @@ int batch_mlem(mc_batch *b, int n_iter, cudaStream_t s) {
     b->exec_iters = n_iter;
   }
   MCS_CUDA(cudaGraphLaunch(b->exec, s));
+  return MC_OK;
+}
+
+// The batched reconstruction with the iterations in one cooperative launch
+// (start images, iterations, write-back: five launches in all).
+int batch_mlem_persistent(mc_batch *b, int n_iter, cudaStream_t s) {
+  int dev = 0, coop = 0, per_sm = 0;
+  MCS_CUDA(cudaGetDevice(&dev));
+  MCS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) { set_error("the device does not support cooperative launches"); return MC_ECUDA; }
+  MCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, kStreamThreads, 0));
+  if (per_sm < 1) { set_error("the persistent batch kernel does not fit on an SM"); return MC_ECUDA; }
+  const BatchSys *sys = b->systems.as<BatchSys>();
+  const unsigned rows = (unsigned)(b->n * kInitChunks);
+  count_launch();
+  batch_init_sums_kernel<<<rows, 256, 0, s>>>(sys, b->part_y.as<double>());
+  count_launch();
+  batch_init_total_kernel<<<div_up(b->n, 256), 256, 0, s>>>(b->part_y.as<double>(), b->part_s.as<double>(), b->n,
+                                                            b->x0.as<double>());
+  count_launch();
+  batch_init_fill_kernel<<<rows, 256, 0, s>>>(sys, b->x0.as<double>());
+  MCS_LAUNCHED();
+  if (n_iter > 0 && (b->n_tiles_fwd || b->n_tiles_bwd)) {
+    // every block resident (a grid-wide barrier needs all of them); no more
+    // blocks than tiles of the larger half
+    uint64_t grid = (uint64_t)per_sm * (uint64_t)device_sm_count();
+    const uint64_t most = std::max(b->n_tiles_fwd, b->n_tiles_bwd);
+    if (grid > most) grid = most;
+    const uint64_t *tf = b->tile_fwd.as<uint64_t>(), *tb = b->tile_bwd.as<uint64_t>();
+    uint64_t nf = b->n_tiles_fwd, nb = b->n_tiles_bwd;
+    int n_sys = b->n, it = n_iter;
+    void *args[] = {(void *)&sys, (void *)&tf, (void *)&nf, (void *)&tb, (void *)&nb, (void *)&n_sys, (void *)&it};
+    count_launch();
+    MCS_CUDA(cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel, dim3((unsigned)grid),
+                                         dim3(kStreamThreads), args, 0, s));
+  }
+  count_launch();
+  batch_scatter_kernel<<<rows, 256, 0, s>>>(sys);
+  MCS_LAUNCHED();
   return MC_OK;
 }
 

@@ -38,7 +38,7 @@ EXPORTED = (
     "mc_project", "mc_backproject", "mc_sensitivity", "mc_mlem_init", "mlem_iterate", "mlem_iterate_noalloc",
     "mc_system_subset", "osem_iterate", "mc_project_ratio", "mc_loglik", "mc_project_f64", "mc_backproject_f64", "mc_prior_quadratic",
     "mc_prior_quadratic_f64", "mc_pgd_step", "mc_system_autotune", "mc_batch_create", "mc_batch_mlem",
-    "mc_batch_free",
+    "mc_batch_free", "mc_batch_mlem_persistent",
     "mc_trace_histories", "mc_debug_kn", "mc_debug_beam", "mc_debug_distance_map", "mc_kernel_launches",
     "mc_last_error",
 )
@@ -136,6 +136,7 @@ def load(path: str | None = None):
             "mc_system_set_spmv_layout": [vp, i32, i32, vp],
             "mc_batch_create": [vp, i32, vp, vp, vp],
             "mc_batch_mlem": [vp, i32, vp],
+            "mc_batch_mlem_persistent": [vp, i32, vp],
             "mc_batch_free": [vp],
             "mc_trace_histories": [vp, vp, u64, u64, u64, vp],
             "mc_debug_kn": [dbl, i32, u64, u64, vp, vp],
@@ -575,6 +576,9 @@ class Batch:
     def mlem(self, n_iter: int, stream=None):
         _check(load().mc_batch_mlem(self._h, int(n_iter), _stream_ptr(stream)))
 
+    def mlem_persistent(self, n_iter: int, stream=None):
+        _check(load().mc_batch_mlem_persistent(self._h, int(n_iter), _stream_ptr(stream)))
+
     def free(self):
         if self._h:
             _check(load().mc_batch_free(self._h))
@@ -595,6 +599,10 @@ def mc_batch_create(systems, ys, xs) -> Batch:
 
 def mc_batch_mlem(batch: Batch, n_iter: int, stream=None):
     batch.mlem(n_iter, stream)
+
+
+def mc_batch_mlem_persistent(batch: Batch, n_iter: int, stream=None):
+    batch.mlem_persistent(n_iter, stream)
 
 
 def mc_batch_free(batch: Batch):

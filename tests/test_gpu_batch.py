@@ -68,6 +68,22 @@ def test_batch_equals_oracle_mlem(batch_env):
     b.free()
 
 
+def test_persistent_batch_equals_oracle_mlem(batch_env):
+    # all iterations in one cooperative launch: the same images
+    import torch
+    mc, mix, systems, ys, cases = batch_env
+    xs = [torch.full((s.shape[1],), 3.0, device="cuda") for s in systems]
+    b = mc.Batch(systems, ys, xs)
+    for n_iter in (30, 1, 0):
+        b.mlem_persistent(n_iter)
+        torch.cuda.synchronize()
+        want = _oracle_images(cases, n_iter)
+        for x, w in zip(xs, want):
+            got = x.cpu().numpy().astype(np.float64)
+            assert _rel_l2(got, w) <= MLEM_TOL
+    b.free()
+
+
 def test_autotune_keeps_results(batch_env):
     import torch
     mc, mix, systems, ys, cases = batch_env
