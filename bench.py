@@ -51,12 +51,12 @@ OPS_PER_EMISSION = 30.0
 ALU_LANES_PER_SM = 128
 # DRAM bytes (read + write) counted by ncu for the present kernels, for the
 # `traffic` fields: transport_kernel<float> in one launch of 1e9 histories of
-# the 128^3 torso (16.30 MB + 987.95 MB: mostly the escape queue, which a
+# the 128^3 torso (13.52 MB + 987.50 MB: mostly the escape queue, which a
 # launch of 1e8 histories keeps in L2), per history; and one ML-EM iteration's
 # forward + back-projection stream kernels on the benchmark's 1e9-history
 # matrix (82.31 + 0.13 MB and 99.61 + 2.61 MB, single-pass capture).  To be
 # taken again (or set to None) whenever those kernels change.
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (16300032 + 987949568) / 1e9
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (13516544 + 987495168) / 1e9
 MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
 
 

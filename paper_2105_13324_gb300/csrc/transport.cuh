@@ -102,11 +102,13 @@ template <typename T> struct FdRec {
 static_assert(sizeof(FdRec<float>) == 48 && sizeof(FdRec<double>) == 80, "forced-detection record layout");
 
 // Philox4x32-10 with precomputed round keys (Salmon et al., SC'11): each
-// round is two 32x32->64 multiplies and two three-way xors.
-__device__ __forceinline__ void philox_rounds(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
-                                              const uint32_t *rk) {
+// round is two 32x32->64 multiplies and two three-way xors.  The R-argument
+// form runs rounds R..9 only, for a caller that has done rounds 0..R-1.
+template <int R>
+__device__ __forceinline__ void philox_rounds_from(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                                   const uint32_t *rk) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
+  for (int r = R; r < 10; ++r) {
     const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
     const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
     const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[2 * r];
@@ -116,6 +118,10 @@ __device__ __forceinline__ void philox_rounds(uint32_t &c0, uint32_t &c1, uint32
     c0 = n0;
     c2 = n2;
   }
+}
+__device__ __forceinline__ void philox_rounds(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                              const uint32_t *rk) {
+  philox_rounds_from<0>(c0, c1, c2, c3, rk);
 }
 
 // One history's stream: block b of history h is counter (b, 0, h_lo, h_hi);
@@ -161,16 +167,33 @@ struct KRng {
 constexpr int kRing = 16;
 constexpr int kRingThreads = 256;
 template <typename T> struct TArgs;
+
+// Ring's Philox: block b's counter is (b, 0, h_lo, h_hi).  Round 0 turns it into
+// (u0, u1, hi(M0 b) ^ h_hi ^ k1_0, lo(M0 b)) with u0 = hi(M1 h_lo) ^ k0_0 and
+// u1 = lo(M1 h_lo), which depend on the history only; round 1 then forms
+// M0 u0, again the history's alone.  start() computes those once per history
+// (hk, e1 = u1 ^ k0_1, f1 = hi(M0 u0) ^ k1_1, d1 = lo(M0 u0)), so a refill
+// does two multiplies for rounds 0 and 1 instead of four; the words are the
+// same as from philox_rounds on the full counter.
 struct Ring {
   uint32_t (*buf)[kRingThreads];
-  uint32_t tid, head, avail, blk, h_lo, h_hi;
-  __device__ __forceinline__ void start(uint64_t h) {
-    h_lo = (uint32_t)h; h_hi = (uint32_t)(h >> 32);
+  uint32_t tid, head, avail, blk;
+  uint32_t hk, e1, f1, d1;
+  __device__ __forceinline__ void start(uint64_t h, const uint32_t *rk) {
+    const uint32_t h_lo = (uint32_t)h, h_hi = (uint32_t)(h >> 32);
     blk = 0; avail = 0; head = 0;
+    const uint64_t m1 = (uint64_t)0xCD9E8D57u * h_lo;
+    const uint64_t m0 = (uint64_t)0xD2511F53u * ((uint32_t)(m1 >> 32) ^ rk[0]);
+    hk = h_hi ^ rk[1];
+    e1 = (uint32_t)m1 ^ rk[2];
+    f1 = (uint32_t)(m0 >> 32) ^ rk[3];
+    d1 = (uint32_t)m0;
   }
   template <typename A> __device__ __forceinline__ void refill(const A &a) {
-    uint32_t c0 = blk, c1 = 0u, c2 = h_lo, c3 = h_hi;
-    philox_rounds(c0, c1, c2, c3, a.rk);
+    const uint64_t p0 = (uint64_t)0xD2511F53u * blk;         // round 0's block-dependent half
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * ((uint32_t)(p0 >> 32) ^ hk);  // round 1
+    uint32_t c0 = (uint32_t)(p1 >> 32) ^ e1, c1 = (uint32_t)p1, c2 = f1 ^ (uint32_t)p0, c3 = d1;
+    philox_rounds_from<2>(c0, c1, c2, c3, a.rk);
     uint32_t *w = &buf[(blk & 3u) << 2][tid];  // four rows from here
     w[0] = c0;
     w[kRingThreads] = c1;
@@ -502,7 +525,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
   rg.buf = s_ring;
   rg.tid = threadIdx.x;
   rg.head = 0;
-  rg.start(a.first + i);
+  rg.start(a.first + i, a.rk);
   T px = 0, py = 0, pz = 0, dx = 0, dy = 0, dz = 1;
   Energy<T> en;
   en.e = en.sig = en.e3 = en.ie3 = (T)0;
@@ -682,7 +705,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       }
       if (i < a.count) {
         st = S_EMIT;
-        rg.start(a.first + i);  // next history's stream
+        rg.start(a.first + i, a.rk);  // next history's stream
       } else {
         st = S_DONE;
       }
