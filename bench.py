@@ -53,11 +53,11 @@ ALU_LANES_PER_SM = 128
 # `traffic` fields: transport_kernel<float> in one launch of 1e9 histories of
 # the 128^3 torso (13.52 MB + 987.50 MB: mostly the escape queue, which a
 # launch of 1e8 histories keeps in L2), per history; and one ML-EM iteration's
-# forward + back-projection stream kernels on the benchmark's 1e9-history
-# matrix (82.31 + 0.13 MB and 99.61 + 2.61 MB, single-pass capture).  To be
+# forward + back-projection warp-chunk kernels on the benchmark's 1e9-history
+# matrix (82.28 + 0.47 MB and 99.59 + 3.53 MB, single-pass capture).  To be
 # taken again (or set to None) whenever those kernels change.
 TRANSPORT_DRAM_BYTES_PER_HISTORY = (13516544 + 987495168) / 1e9
-MLEM_DRAM_BYTES_PER_ITER_1E9 = 82313216 + 134656 + 99606528 + 2612992
+MLEM_DRAM_BYTES_PER_ITER_1E9 = 82283776 + 470784 + 99588864 + 3533568
 
 
 # Nominal issue rates per SM and clock of the pipes the transport kernel
@@ -904,7 +904,9 @@ def run_ours(args, w):
                               "traffic": (MLEM_DRAM_BYTES_PER_ITER_1E9
                                           if w.name == "torso128" and H == 10 ** 9 else None),
                               "bytes_per_iter": mlem_bytes, "peak_kind": peak_kind,
-                              "note": "benchmark matrix (largely L2-resident)"},
+                              "note": "benchmark matrix; rows of ~3.7 entries: bound by the L1-to-L2 request "
+                                      "rate of the vector gathers (one 32-byte request per entry), not by DRAM "
+                                      "bytes"},
             "roofline_mlem_roof": roof,
             "serving": serving,
             "forced_detection": fd,

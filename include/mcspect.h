@@ -148,7 +148,7 @@ typedef struct mc_system_info {
   double build_ms_transport; /* device time of the build's transport kernel */
   double build_ms_assembly;  /* ... of matrix assembly (sort, CSR/CSC, sums) */
   double build_ms_detect;    /* ... of the collimator/detector kernel */
-  int32_t spmv_fwd, spmv_bwd; /* projector kernels: 0 = streaming tiles,
+  int32_t spmv_fwd, spmv_bwd; /* projector kernels: 0 = streaming layout,
                                  else lanes per row (column) group */
   int32_t weighted;           /* 1: entries are summed forced-detection
                                  weights (counts = weighted events per entry) */
@@ -283,12 +283,14 @@ MC_API int mc_system_export_csr(const mc_system *sys, int64_t *row_ptr_host, int
 MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t allow_rounding);
 
 /* Projector kernels of a system: fwd (forward projection, CSR) and bwd
- * (back-projection, CSC) each 0 = streaming tiles (entries of runs of whole
- * rows staged in shared memory, then one fixed-order sum per row), 1, 2, 4,
- * 8, 16 or 32 = that many lanes per row (column), or -1 = keep.  Every
- * layout gives the same sums up to FP32 rounding order.  Streaming tiles
- * need every row (column) shorter than 2048 entries: MC_EINVAL otherwise
- * (the system is left unchanged).  Synchronises `stream`. */
+ * (back-projection, CSC) each 0 = streaming layout (entries of runs of whole
+ * rows staged in shared memory, then one fixed-order sum per row: one lane
+ * per row in warps of 32 rows when rows average fewer than 16 entries, else
+ * one warp per row in tiles of ~4096 entries), 1, 2, 4, 8, 16 or 32 = that
+ * many lanes per row (column), or -1 = keep.  Every layout gives the same
+ * sums up to FP32 rounding order.  The streaming layout needs every row
+ * (column) shorter than 2048 entries: MC_EINVAL otherwise (the system is
+ * left unchanged).  Synchronises `stream`. */
 MC_API int mc_system_set_spmv_layout(mc_system *sys, int32_t fwd, int32_t bwd, void *stream);
 
 /* Forward projection q = A x (Eq. (IMC)): x_dev[N], q_dev[M], float. */
@@ -390,7 +392,7 @@ MC_API int mc_pgd_step(int64_t n, double alpha, const double *sens_dev, const fl
                        float *x_dev, void *stream);
 
 /* SpMV autotuner: times the forward and back-projection kernels of `sys`
- * (streaming tiles, row groups of 1..32 lanes) on its own matrix and keeps
+ * (streaming layout, row groups of 1..32 lanes) on its own matrix and keeps
  * the fastest of each (reported by mc_system_info_get).  Synchronises. */
 MC_API int mc_system_autotune(mc_system *sys, void *stream);
 
@@ -401,7 +403,7 @@ MC_API int mc_system_autotune(mc_system *sys, void *stream);
  * (mc_mlem_init) and runs n_iter updates of Eq. (MLEM) for all of them: one
  * forward and one back-projection launch per iteration over all systems,
  * captured once into a CUDA graph per n_iter and replayed.  Every system
- * must be a full FP32 system with streaming tiles (short rows, as MC
+ * must be a full FP32 system with the streaming layout (short rows, as MC
  * matrices of moderate history counts have); results equal mlem_iterate's.
  * Systems in a batch must not be used by other calls while it runs. */
 typedef struct mc_batch mc_batch;

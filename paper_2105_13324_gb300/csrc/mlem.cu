@@ -250,8 +250,10 @@ __global__ void sensitivity_kernel(const double *colsum, const uint32_t *n_v, in
 // CSR (CSC) arrays.  The block first reads the tile's entries and gathers the
 // vector with independent, coalesced loads (many requests in flight), keeps
 // the products in shared memory, and then reduces each row from shared
-// memory: one thread per row for short rows, one warp per row for long ones.
-// Every row is summed in a fixed order, so results are reproducible.
+// memory: one warp per row (segments of 16 or more entries on average), or
+// one thread per row (the batch kernels).  Single systems with shorter
+// segments use the warp chunks below instead.  Every row is summed in a fixed
+// order, so results are reproducible.
 constexpr int kStreamTile = 4096;
 constexpr int kStreamThreads = 256;
 
@@ -442,6 +444,93 @@ __global__ void __launch_bounds__(kStreamThreads) stream_back_kernel(const uint3
   stream_segments<WARP>(col_ptr, c0, c1, p0, s_prod, o);
 }
 
+// ---------------------------------------------------------------------------
+// warp chunks: short segments, one lane per segment, no block barrier
+// ---------------------------------------------------------------------------
+// Warp w takes segments [32 w, 32 w + 32), lane l segment 32 w + l.  The
+// chunk's entries are contiguous; the warp reads them in windows of
+// kChunkWindow (coalesced index and value loads, then one gather per entry),
+// keeps the window's products in its own shared-memory row, and each lane
+// adds up its segment's part of the window in entry order.  A segment is
+// therefore summed in the same order, from the same products, as by a plain
+// loop over its entries (and as by the thread-per-row tiles), and segments of
+// any length are handled.  Blocks are small so that few warp slots wait for
+// the slowest warp of a block.
+constexpr int kChunkWindow = 128;
+constexpr int kChunkThreads = 128;
+
+template <typename V, typename Out>
+__device__ __forceinline__ void chunk_segments(const uint32_t *__restrict__ ptr, int64_t n_seg,
+                                               const uint32_t *__restrict__ idx, const V *__restrict__ val,
+                                               const float *__restrict__ vec, float *s_w, Out &out) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t j = (int64_t)blockIdx.x * kChunkThreads + threadIdx.x;
+  const bool mine = j < n_seg;
+  const uint32_t b = ptr[mine ? j : n_seg], e = ptr[mine ? j + 1 : n_seg];
+  typename Out::Pre pre{};
+  if (mine) pre = out.load((uint32_t)j);
+  // the chunk's entries [p0, p1): lane 0's first to lane 31's last
+  const uint32_t p0 = __shfl_sync(0xffffffffu, b, 0), p1 = __shfl_sync(0xffffffffu, e, 31);
+  float acc = 0.0f;
+  for (uint32_t w0 = p0; w0 < p1; w0 += kChunkWindow) {
+    const uint32_t n = min((uint32_t)kChunkWindow, p1 - w0);
+    uint32_t c[kChunkWindow / 32];
+    float v[kChunkWindow / 32];
+#pragma unroll
+    for (int u = 0; u < kChunkWindow / 32; ++u) {
+      const uint32_t k = lane + 32u * u;
+      c[u] = 0u;
+      v[u] = 0.0f;
+      if (k < n) {
+        c[u] = __ldcs(idx + w0 + k);
+        v[u] = to_f(__ldcs(val + w0 + k));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kChunkWindow / 32; ++u) {
+      const uint32_t k = lane + 32u * u;
+      if (k < n) s_w[k] = v[u] * __ldg(vec + c[u]);
+    }
+    __syncwarp();
+    const uint32_t lo = b > w0 ? b : w0, hi = e < w0 + n ? e : w0 + n;
+    for (uint32_t k = lo; k < hi; ++k) acc += s_w[k - w0];
+    __syncwarp();
+  }
+  if (mine) out.store((uint32_t)j, acc, pre, e > b);
+}
+
+template <typename V, int MODE, bool LL>
+__global__ void __launch_bounds__(kChunkThreads) chunk_forward_kernel(const uint32_t *__restrict__ row_ptr, int64_t m,
+                                                                   const uint32_t *__restrict__ col,
+                                                                   const V *__restrict__ val,
+                                                                   const float *__restrict__ xs,
+                                                                   const float *__restrict__ y,
+                                                                   float *__restrict__ out, double *partials,
+                                                                   const uint32_t *__restrict__ rmap,
+                                                                   const float *__restrict__ add) {
+  __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
+  __shared__ double s_tmp[kChunkThreads / 32];
+  FwdOut<MODE, LL> o{y, out, rmap, add, 0.0};
+  chunk_segments<V>(row_ptr, m, col, val, xs, s_w[threadIdx.x >> 5], o);
+  if (LL) {
+    const double t = block_sum_double(o.ll, s_tmp);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+template <typename V, int MODE>
+__global__ void __launch_bounds__(kChunkThreads) chunk_back_kernel(const uint32_t *__restrict__ col_ptr, int64_t n,
+                                                                const uint32_t *__restrict__ row,
+                                                                const V *__restrict__ val,
+                                                                const float *__restrict__ r,
+                                                                const float *__restrict__ inv_n,
+                                                                const float *__restrict__ inv_colsum,
+                                                                float *__restrict__ x, float *__restrict__ xs) {
+  __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
+  BackOut<MODE> o{inv_n, inv_colsum, x, xs};
+  chunk_segments<V>(col_ptr, n, row, val, r, s_w[threadIdx.x >> 5], o);
+}
+
 // longest segment of a CSR/CSC pointer array
 __global__ void max_segment_kernel(const uint32_t *ptr, int64_t n, unsigned int *out) {
   uint32_t mx = 0;
@@ -530,8 +619,8 @@ static void stream_fwd_launch(const mc_system *sys, const float *xs, const float
     stream_forward_kernel<V, true, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials,
                                                                             rmap, add);
   else
-    stream_forward_kernel<V, false, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials,
-                                                                             rmap, add);
+    chunk_forward_kernel<V, MODE, LL><<<(unsigned)div_up(sys->n_rows, kChunkThreads), kChunkThreads, 0, s>>>(
+        rp, sys->n_rows, ci, val, xs, y, out, partials, rmap, add);
 }
 
 template <typename V, int MODE>
@@ -544,7 +633,8 @@ static void stream_back_launch(const mc_system *sys, const float *r, float *x, f
   if (sys->warp_rows_bwd)
     stream_back_kernel<V, true, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
   else
-    stream_back_kernel<V, false, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
+    chunk_back_kernel<V, MODE><<<(unsigned)div_up(sys->n_cols, kChunkThreads), kChunkThreads, 0, s>>>(
+        cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
 }
 
 template <int MODE, bool LL>
@@ -578,6 +668,7 @@ static void back_dispatch(const mc_system *sys, const float *r, float *x, float 
 }
 
 int forward_blocks(const mc_system *sys) {
+  if (sys->n_csr_blocks > 0 && !sys->warp_rows_fwd) return div_up(sys->n_rows, kChunkThreads);  // warp chunks
   if (sys->n_csr_blocks > 0) return (int)sys->n_csr_blocks;
   return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads);
 }

@@ -544,7 +544,7 @@ def mc_pgd_step(alpha: float, sens, bp, x, gp=None, stream=None):
 
 
 def mc_system_set_spmv_layout(sys: System, fwd: int, bwd: int, stream=None):
-    """Projector layouts: 0 streaming tiles, 1..32 lanes per row (column)
+    """Projector layouts: 0 streaming layout, 1..32 lanes per row (column)
     group, -1 keep; returns the layouts now in use."""
     _check(load().mc_system_set_spmv_layout(sys.handle, int(fwd), int(bwd), _stream_ptr(stream)))
     i = sys.info()

@@ -2,7 +2,8 @@
 oracle on the same matrix (paper Sec. 5.1, Eq. (MLEM) on the matrix of
 Eq. (IMC)), through the C ABI.
 
-The layouts are forced with mc_system_set_spmv_layout: streaming tiles, and
+The layouts are forced with mc_system_set_spmv_layout: the streaming layout
+(warp chunks for short rows, tiles of one warp per row for longer ones), and
 row (column) groups of 1..32 lanes.  The matrices are oracle-side count
 matrices built from seeded synthetic tallies: long rows and columns (200 to
 745 entries per row, as the 10^11-history instance of the 128^3 workload
@@ -212,7 +213,7 @@ def test_mlem_on_a_system_of_the_128_cubed_size_class(mc):
     y = P.poisson_counts(a @ np.ones(n_cols), 2e7, 42)
     want = oracle.mlem(a, y, oracle.mlem_init(a, y), 50)
     sysm = mc.mc_system_from_events(n_rows, n_cols, rows, cols, 0, H)
-    assert sysm.info()["spmv_fwd"] == 0 and sysm.info()["spmv_bwd"] == 0   # streaming tiles by default
+    assert sysm.info()["spmv_fwd"] == 0 and sysm.info()["spmv_bwd"] == 0   # streaming layout (warp chunks) by default
     yd = torch.as_tensor(y).cuda()
     for layout in (0, 4):
         mc.mc_system_set_spmv_layout(sysm, layout, layout)
@@ -223,3 +224,61 @@ def test_mlem_on_a_system_of_the_128_cubed_size_class(mc):
         assert _rel_l2(got, want) <= MLEM_TOL
         np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-6 * float(want.max()))
     sysm.free()
+
+
+@pytest.fixture(scope="module")
+def short_rows_ragged(mc):
+    # short rows and columns (the default streaming layout: one lane per
+    # segment, 32 segments per warp, entries read in windows of 128) with the
+    # awkward cases spelled out: 5013 rows and 3001 columns (the last chunk
+    # of either is partial), half the rows empty and a run of 96 empty rows
+    # (whole empty chunks), one row of 700 entries (several windows), two
+    # rows of 150 entries at a chunk boundary (a window boundary inside a
+    # row), a column of 600 entries and a run of empty columns
+    n_rows, n_cols = 5013, 3001
+    rows, cols = P.random_events(n_rows, n_cols, (0, 6), 3, seed=51, rows_used=0.5)
+    keep = ~((rows >= 1000) & (rows < 1096)) & ~((cols >= 2000) & (cols < 2100))
+    rows, cols = rows[keep], cols[keep]
+    rng = np.random.Generator(np.random.Philox(52))
+    outside = np.setdiff1d(np.arange(n_rows), np.arange(1000, 1096))
+    extra_r = [np.full(700, 77), np.full(150, 2015), np.full(150, 2016), rng.choice(outside, 600, replace=False),
+               np.array([n_rows - 1])]
+    extra_c = [rng.choice(2000, 700, replace=False), rng.choice(2000, 150, replace=False),
+               rng.choice(2000, 150, replace=False), np.full(600, 7), np.array([n_cols - 1])]
+    rows = np.concatenate([rows] + extra_r).astype(np.int32)
+    cols = np.concatenate([cols] + extra_c).astype(np.int32)
+    return _Case(mc, n_rows, n_cols, rows, cols, 4 * n_cols + 3, seed=53)
+
+
+def test_short_segment_layout_edge_cases_match_oracle(mc, short_rows_ragged):
+    import torch
+    case = short_rows_ragged
+    inf = case.sysm.info()
+    assert inf["spmv_fwd"] == 0 and inf["spmv_bwd"] == 0
+    assert case.c.nnz / case.n_rows < 16 and case.c.nnz / case.n_cols < 16   # one lane per segment
+    a = case.a.tocsr()
+    x = np.linspace(0.5, 2.0, case.n_cols)
+    xd = torch.as_tensor(x.astype(np.float32)).cuda()
+    q = torch.zeros(case.n_rows, dtype=torch.float32, device="cuda")
+    mc.mc_project(case.sysm, xd, q)
+    q_want = a @ x.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(q.cpu().numpy(), q_want, rtol=1e-6, atol=1e-7 * q_want.max())
+    assert np.all(q.cpu().numpy()[np.diff(a.indptr) == 0] == 0.0)          # empty rows project to 0
+    r = np.linspace(0.0, 3.0, case.n_rows)
+    b = torch.zeros(case.n_cols, dtype=torch.float32, device="cuda")
+    mc.mc_backproject(case.sysm, torch.as_tensor(r.astype(np.float32)).cuda(), b)
+    b_want = a.T @ r.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(b.cpu().numpy(), b_want, rtol=1e-6, atol=1e-7 * b_want.max())
+    rd = torch.zeros(case.n_rows, dtype=torch.float32, device="cuda")
+    mc.mc_project_ratio(case.sysm, xd, case.yd, rd)
+    ratio = np.divide(case.y, q_want, out=np.zeros_like(q_want), where=q_want > 0)
+    np.testing.assert_allclose(rd.cpu().numpy(), ratio, rtol=1e-5, atol=1e-6 * ratio.max())
+    # log-likelihood through the forward kernel's per-block partials
+    ll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mc.mc_loglik(case.sysm, xd, case.yd, ll)
+    ll_want = oracle.loglik(a, x.astype(np.float32), case.y)
+    assert abs(float(ll[0]) - ll_want) <= 1e-6 * abs(ll_want)
+    for vt in ("f32", "f16", "bf16"):
+        case.sysm.set_value_type(vt)
+        _check_image(case.gpu_image(mc), case.oracle_image(case.a))
+    case.sysm.set_value_type("f32")

@@ -366,7 +366,7 @@ def test_reduced_precision_values_exact_counts(mc, torso_small, vt):
 
 
 def test_half_and_float_values_give_identical_images():
-    # short rows (streaming tiles): counts <= 2048 are exact in half, the
+    # short rows (streaming layout): counts <= 2048 are exact in half, the
     # products are formed in float either way and every segment is summed in
     # the same order, so images, log-likelihoods and back-projections must be
     # identical bit for bit
