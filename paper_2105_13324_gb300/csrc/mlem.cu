@@ -447,31 +447,55 @@ __global__ void __launch_bounds__(kStreamThreads) stream_back_kernel(const uint3
 // ---------------------------------------------------------------------------
 // warp chunks: short segments, one lane per segment, no block barrier
 // ---------------------------------------------------------------------------
-// Warp w takes segments [32 w, 32 w + 32), lane l segment 32 w + l.  The
-// chunk's entries are contiguous; the warp reads them in windows of
-// kChunkWindow (coalesced index and value loads, then one gather per entry),
-// keeps the window's products in its own shared-memory row, and each lane
-// adds up its segment's part of the window in entry order.  A segment is
-// therefore summed in the same order, from the same products, as by a plain
-// loop over its entries (and as by the thread-per-row tiles), and segments of
-// any length are handled.  Blocks are small so that few warp slots wait for
-// the slowest warp of a block.
+// A warp takes the 32 R consecutive segments [j0, j0 + 32 R), lane l the
+// segments j0 + l + 32 r (r < R), so that pointer loads and result stores
+// stay coalesced.  The chunk's entries are contiguous; the warp reads them in
+// windows of kChunkWindow (coalesced index and value loads, then one gather
+// per entry), keeps the window's products in its own shared-memory row, and
+// each lane adds up its segments' parts of the window in entry order.  A
+// segment is therefore summed in the same order, from the same products, as
+// by a plain loop over its entries, and segments of any length are handled.
+// R (1, 2, 4) is chosen so that a chunk holds about 100 entries or more
+// (very short segments leave too few gathers in flight per warp otherwise),
+// but no larger than keeps 32 warps per SM in the launch (small launches
+// need the warps more than the longer chunks).
+// Blocks are small so that few warp slots wait for the slowest warp of a
+// block.
 constexpr int kChunkWindow = 128;
 constexpr int kChunkThreads = 128;
+static_assert(kStreamTile >= (kStreamThreads / 32) * kChunkWindow, "a tile block's products hold its warps' windows");
 
-template <typename V, typename Out>
+// Segments per lane for n segments averaging nnz / n entries, in a launch
+// over `launch_segments` segments in all.
+inline int chunk_rows_per_lane(int64_t nnz, int64_t n, int64_t launch_segments) {
+  int r = (double)nnz >= 3.0 * (double)n ? 1 : (double)nnz >= 1.5 * (double)n ? 2 : 4;
+  const int64_t min_warps = (int64_t)device_sm_count() * 32;
+  while (r > 1 && launch_segments / (32 * r) < min_warps) r >>= 1;
+  return r;
+}
+
+// j0: the warp's first segment (a multiple of 32 R); s_w: the warp's
+// kChunkWindow floats.
+template <int R, typename V, typename Out>
 __device__ __forceinline__ void chunk_segments(const uint32_t *__restrict__ ptr, int64_t n_seg,
                                                const uint32_t *__restrict__ idx, const V *__restrict__ val,
-                                               const float *__restrict__ vec, float *s_w, Out &out) {
+                                               const float *__restrict__ vec, float *s_w, Out &out, int64_t j0) {
   const uint32_t lane = threadIdx.x & 31u;
-  const int64_t j = (int64_t)blockIdx.x * kChunkThreads + threadIdx.x;
-  const bool mine = j < n_seg;
-  const uint32_t b = ptr[mine ? j : n_seg], e = ptr[mine ? j + 1 : n_seg];
-  typename Out::Pre pre{};
-  if (mine) pre = out.load((uint32_t)j);
+  uint32_t b[R], e[R];
+  typename Out::Pre pre[R];
+  float acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t j = j0 + lane + 32 * r;
+    const bool mine = j < n_seg;
+    b[r] = ptr[mine ? j : n_seg];
+    e[r] = ptr[mine ? j + 1 : n_seg];
+    pre[r] = typename Out::Pre{};
+    if (mine) pre[r] = out.load((uint32_t)j);
+    acc[r] = 0.0f;
+  }
   // the chunk's entries [p0, p1): lane 0's first to lane 31's last
-  const uint32_t p0 = __shfl_sync(0xffffffffu, b, 0), p1 = __shfl_sync(0xffffffffu, e, 31);
-  float acc = 0.0f;
+  const uint32_t p0 = __shfl_sync(0xffffffffu, b[0], 0), p1 = __shfl_sync(0xffffffffu, e[R - 1], 31);
   for (uint32_t w0 = p0; w0 < p1; w0 += kChunkWindow) {
     const uint32_t n = min((uint32_t)kChunkWindow, p1 - w0);
     uint32_t c[kChunkWindow / 32];
@@ -492,14 +516,26 @@ __device__ __forceinline__ void chunk_segments(const uint32_t *__restrict__ ptr,
       if (k < n) s_w[k] = v[u] * __ldg(vec + c[u]);
     }
     __syncwarp();
-    const uint32_t lo = b > w0 ? b : w0, hi = e < w0 + n ? e : w0 + n;
-    for (uint32_t k = lo; k < hi; ++k) acc += s_w[k - w0];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t lo = b[r] > w0 ? b[r] : w0, hi = e[r] < w0 + n ? e[r] : w0 + n;
+      for (uint32_t k = lo; k < hi; ++k) acc[r] += s_w[k - w0];
+    }
     __syncwarp();
   }
-  if (mine) out.store((uint32_t)j, acc, pre, e > b);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t j = j0 + lane + 32 * r;
+    if (j < n_seg) out.store((uint32_t)j, acc[r], pre[r], e[r] > b[r]);
+  }
 }
 
-template <typename V, int MODE, bool LL>
+// the warp's first segment in the single-system kernels
+template <int R> __device__ __forceinline__ int64_t chunk_first() {
+  return ((int64_t)blockIdx.x * kChunkThreads + (threadIdx.x & ~31u)) * R;
+}
+
+template <int R, typename V, int MODE, bool LL>
 __global__ void __launch_bounds__(kChunkThreads) chunk_forward_kernel(const uint32_t *__restrict__ row_ptr, int64_t m,
                                                                    const uint32_t *__restrict__ col,
                                                                    const V *__restrict__ val,
@@ -511,14 +547,14 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_forward_kernel(const uint
   __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
   __shared__ double s_tmp[kChunkThreads / 32];
   FwdOut<MODE, LL> o{y, out, rmap, add, 0.0};
-  chunk_segments<V>(row_ptr, m, col, val, xs, s_w[threadIdx.x >> 5], o);
+  chunk_segments<R, V>(row_ptr, m, col, val, xs, s_w[threadIdx.x >> 5], o, chunk_first<R>());
   if (LL) {
     const double t = block_sum_double(o.ll, s_tmp);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
-template <typename V, int MODE>
+template <int R, typename V, int MODE>
 __global__ void __launch_bounds__(kChunkThreads) chunk_back_kernel(const uint32_t *__restrict__ col_ptr, int64_t n,
                                                                 const uint32_t *__restrict__ row,
                                                                 const V *__restrict__ val,
@@ -528,7 +564,7 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_back_kernel(const uint32_
                                                                 float *__restrict__ x, float *__restrict__ xs) {
   __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
   BackOut<MODE> o{inv_n, inv_colsum, x, xs};
-  chunk_segments<V>(col_ptr, n, row, val, r, s_w[threadIdx.x >> 5], o);
+  chunk_segments<R, V>(col_ptr, n, row, val, r, s_w[threadIdx.x >> 5], o, chunk_first<R>());
 }
 
 // longest segment of a CSR/CSC pointer array
@@ -618,9 +654,19 @@ static void stream_fwd_launch(const mc_system *sys, const float *xs, const float
   if (sys->warp_rows_fwd)
     stream_forward_kernel<V, true, MODE, LL><<<nb, kStreamThreads, 0, s>>>(rp, t, ci, val, xs, y, out, partials,
                                                                             rmap, add);
-  else
-    chunk_forward_kernel<V, MODE, LL><<<(unsigned)div_up(sys->n_rows, kChunkThreads), kChunkThreads, 0, s>>>(
-        rp, sys->n_rows, ci, val, xs, y, out, partials, rmap, add);
+  else {
+    const int R = chunk_rows_per_lane(sys->nnz, sys->n_rows, sys->n_rows);
+    const unsigned g = (unsigned)div_up(sys->n_rows, (int64_t)kChunkThreads * R);
+    if (R == 1)
+      chunk_forward_kernel<1, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
+                                                                     rmap, add);
+    else if (R == 2)
+      chunk_forward_kernel<2, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
+                                                                     rmap, add);
+    else
+      chunk_forward_kernel<4, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
+                                                                     rmap, add);
+  }
 }
 
 template <typename V, int MODE>
@@ -632,9 +678,16 @@ static void stream_back_launch(const mc_system *sys, const float *r, float *x, f
   count_launch();
   if (sys->warp_rows_bwd)
     stream_back_kernel<V, true, MODE><<<nb, kStreamThreads, 0, s>>>(cp, t, ri, val, r, inv_n, ics, x, xs);
-  else
-    chunk_back_kernel<V, MODE><<<(unsigned)div_up(sys->n_cols, kChunkThreads), kChunkThreads, 0, s>>>(
-        cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
+  else {
+    const int R = chunk_rows_per_lane(sys->nnz, sys->n_cols, sys->n_cols);
+    const unsigned g = (unsigned)div_up(sys->n_cols, (int64_t)kChunkThreads * R);
+    if (R == 1)
+      chunk_back_kernel<1, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
+    else if (R == 2)
+      chunk_back_kernel<2, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
+    else
+      chunk_back_kernel<4, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
+  }
 }
 
 template <int MODE, bool LL>
@@ -668,7 +721,8 @@ static void back_dispatch(const mc_system *sys, const float *r, float *x, float 
 }
 
 int forward_blocks(const mc_system *sys) {
-  if (sys->n_csr_blocks > 0 && !sys->warp_rows_fwd) return div_up(sys->n_rows, kChunkThreads);  // warp chunks
+  if (sys->n_csr_blocks > 0 && !sys->warp_rows_fwd)  // warp chunks
+    return div_up(sys->n_rows, (int64_t)kChunkThreads * chunk_rows_per_lane(sys->nnz, sys->n_rows, sys->n_rows));
   if (sys->n_csr_blocks > 0) return (int)sys->n_csr_blocks;
   return div_up(sys->n_rows * sys->spmv_group_fwd, kSpmvThreads);
 }
@@ -1154,9 +1208,12 @@ int pgd_step(int64_t n, double alpha, const double *sens, const float *bp, const
 // ---------------------------------------------------------------------------
 // batched ML-EM over many systems (serving many acquisitions at once)
 // ---------------------------------------------------------------------------
-// Each iteration is one forward launch over the concatenated CSR tiles of
-// all systems and one back-projection launch over their CSC tiles; a block
-// finds its system by binary search in the prefix of tile counts.  The
+// Each iteration is one forward launch over the concatenated CSR work units
+// of all systems and one back-projection launch over their CSC units; a
+// block finds its system by binary search in the prefix of unit counts.  A
+// unit is 256 R consecutive rows (columns) as eight warp chunks, or, for a
+// system whose rows (columns) average 16 or more entries, one tile with a
+// warp per row (column).  The
 // whole reconstruction (start images, n_iter iterations, write-back of the
 // images) is captured once in a CUDA graph and replayed.
 //
@@ -1173,7 +1230,8 @@ namespace mcs {
 
 struct BatchSys {
   // compacted CSR: segment j is row row_id[j], entries [row_ptr[j],
-  // row_ptr[j + 1]) with column indices in compacted column numbering
+  // row_ptr[j + 1]) with column indices in compacted column numbering;
+  // tiles only where warp_fwd (warp_bwd) is set
   const uint32_t *row_ptr, *row_id, *csr_tiles, *col_idx;
   // compacted CSC: segment j is column col_id[j]; row indices compacted
   const uint32_t *col_ptr, *col_id, *csc_tiles, *row_idx;
@@ -1184,7 +1242,8 @@ struct BatchSys {
   float *x_c, *xs_c;         // per non-empty column: image, image / n_v
   const float *ics_c, *invn_c;  // per non-empty column: 1 / S_v, 1 / n_v
   int64_t n_rows, n_cols, m_c, n_c;
-  int warp_fwd, warp_bwd;
+  int warp_fwd, warp_bwd;  // tiles with a warp per segment, else warp chunks
+  int rpl_fwd, rpl_bwd;    // warp chunks: segments per lane
 };
 
 __device__ __forceinline__ int batch_find(const uint64_t *off, int n, uint64_t i) {
@@ -1218,6 +1277,20 @@ struct BatchFwdOut {
   __device__ __forceinline__ void store(uint32_t j, float acc, float yv, bool) const { r[j] = acc > 0.0f ? yv / acc : 0.0f; }
 };
 
+// Unit u of a warp-chunk system: its block's warps take the chunks of
+// segments [256 R u, 256 R (u + 1)).
+template <typename Out>
+__device__ __forceinline__ void batch_chunks(const uint32_t *__restrict__ ptr, int64_t n_seg,
+                                             const uint32_t *__restrict__ idx, const float *__restrict__ val,
+                                             const float *__restrict__ vec, float *s_prod, Out &o, uint32_t u,
+                                             int R) {
+  float *s_w = s_prod + (threadIdx.x >> 5) * kChunkWindow;
+  const int64_t j0 = ((int64_t)u * kStreamThreads + (threadIdx.x & ~31u)) * R;
+  if (R == 1) chunk_segments<1, float>(ptr, n_seg, idx, val, vec, s_w, o, j0);
+  else if (R == 2) chunk_segments<2, float>(ptr, n_seg, idx, val, vec, s_w, o, j0);
+  else chunk_segments<4, float>(ptr, n_seg, idx, val, vec, s_w, o, j0);
+}
+
 // One forward (ratio) tile and one back-projection (EM update) tile of the
 // batch, by global tile index t
 __device__ __forceinline__ void batch_forward_tile(const BatchSys *__restrict__ systems,
@@ -1226,13 +1299,16 @@ __device__ __forceinline__ void batch_forward_tile(const BatchSys *__restrict__ 
   uint32_t tile;
   const BatchSys &S = batch_desc(systems, tile_off, n_sys, s_desc, t, tile);
   const uint32_t *__restrict__ ptr = S.row_ptr;
+  BatchFwdOut o{S.y_c, S.r_c};
+  if (!S.warp_fwd) {  // warp chunks over rows [256 R u, 256 R (u + 1))
+    batch_chunks(ptr, S.m_c, S.col_idx, S.csr_val, S.xs_c, s_prod, o, tile, S.rpl_fwd);
+    return;
+  }
   const uint32_t j0 = S.csr_tiles[tile], j1 = S.csr_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
   stream_products<float>(p0, ptr[j1] - p0, S.col_idx, S.csr_val, S.xs_c, s_prod);
   __syncthreads();
-  BatchFwdOut o{S.y_c, S.r_c};
-  if (S.warp_fwd) stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
-  else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
+  stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
 }
 
 __device__ __forceinline__ void batch_back_tile(const BatchSys *__restrict__ systems,
@@ -1241,13 +1317,16 @@ __device__ __forceinline__ void batch_back_tile(const BatchSys *__restrict__ sys
   uint32_t tile;
   const BatchSys &S = batch_desc(systems, tile_off, n_sys, s_desc, t, tile);
   const uint32_t *__restrict__ ptr = S.col_ptr;
+  BackOut<1> o{S.invn_c, S.ics_c, S.x_c, S.xs_c};
+  if (!S.warp_bwd) {  // warp chunks over columns [256 R u, 256 R (u + 1))
+    batch_chunks(ptr, S.n_c, S.row_idx, S.csc_val, S.r_c, s_prod, o, tile, S.rpl_bwd);
+    return;
+  }
   const uint32_t j0 = S.csc_tiles[tile], j1 = S.csc_tiles[tile + 1];
   const uint32_t p0 = ptr[j0];
   stream_products<float>(p0, ptr[j1] - p0, S.row_idx, S.csc_val, S.r_c, s_prod);
   __syncthreads();
-  BackOut<1> o{S.invn_c, S.ics_c, S.x_c, S.xs_c};
-  if (S.warp_bwd) stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
-  else stream_segments<false>(ptr, j0, j1, p0, s_prod, o);
+  stream_segments<true>(ptr, j0, j1, p0, s_prod, o);
 }
 
 __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const BatchSys *__restrict__ systems,
@@ -1417,9 +1496,11 @@ struct mc_batch {
 
 namespace mcs {
 
-// The non-empty segments of (ptr, n): their ids, compacted pointers and
-// stream tiles, and `relabel_out` = `relabel_in` (nnz indices into this
-// numbering, from the other orientation) in compacted numbering.
+// The non-empty segments of (ptr, n): their ids, compacted pointers, stream
+// tiles (`warp` set, when segments average 16 or more entries; warp-chunk
+// units are set by batch_create), and `relabel_out` = `relabel_in` (nnz
+// indices into this numbering, from the other orientation) in compacted
+// numbering.
 // `scratch` holds 2 (n + 1) words.
 static int batch_segments(const uint32_t *ptr, int64_t n, int64_t nnz, const uint32_t *relabel_in, uint32_t *scratch,
                           DevBuf &id, DevBuf &cptr, DevBuf &tiles, DevBuf &relabel_out, int64_t &count, int64_t &n_tiles,
@@ -1448,9 +1529,10 @@ static int batch_segments(const uint32_t *ptr, int64_t n, int64_t nnz, const uin
   n_tiles = 0;
   warp = 0;
   if (cnt == 0) return MC_OK;
+  if ((double)nnz / (double)cnt < 16.0) return MC_OK;  // warp chunks: units set by batch_create
   bool w = false;
   MCS_TRY(stream_tiles(cptr, cnt, nnz, tiles, n_tiles, w, s, true));
-  warp = w ? 1 : 0;
+  warp = 1;
   return MC_OK;
 }
 
@@ -1468,8 +1550,9 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
   for (int k = 0; k < n; ++k) {
     const mc_system *s = sys[k];
     if (!s || !y[k] || !x[k]) { set_error("batch entry %d: NULL system or vector", k); return MC_EINVAL; }
-    // the batch builds its own tiles over the non-empty rows and columns
-    // (an error if a row or column is longer than half a tile)
+    // the batch builds its own work units over the non-empty rows and
+    // columns (with tiles, an error if a row or column is longer than half
+    // a tile)
     if (s->value_type != MC_VAL_F32 || s->row_map.p) {
       set_error("batch entry %d: needs a full (not ordered-subset) system with FP32 values", k);
       return MC_EINVAL;
@@ -1518,11 +1601,32 @@ int batch_create(mc_system *const *sys, int n, const float *const *y, float *con
       d.y_c = o[8].as<float>(); d.r_c = o[9].as<float>(); d.x_c = o[10].as<float>(); d.xs_c = o[11].as<float>();
       d.ics_c = o[12].as<float>(); d.invn_c = o[13].as<float>();
       d.n_rows = m->n_rows; d.n_cols = m->n_cols; d.m_c = m_c; d.n_c = n_c;
-      tf[k + 1] = tf[k] + (uint64_t)nt_f;
-      tb[k + 1] = tb[k] + (uint64_t)nt_b;
+      d.rpl_fwd = d.rpl_bwd = 1;
+      tf[k + 1] = (uint64_t)nt_f;  // tiles; warp-chunk units below
+      tb[k + 1] = (uint64_t)nt_b;
       h_colsum[k] = m->colsum.as<double>(); h_nv[k] = m->n_v.as<uint32_t>(); h_ncols[k] = m->n_cols;
     }
     MCS_CUDA(cudaStreamSynchronize(s));  // scratch is released on s after the last compaction
+  }
+  // warp-chunk systems: blocks of 256 R segments, R from the system's mean
+  // segment length and the whole launch's segment count
+  int64_t all_rows = 0, all_cols = 0;
+  for (int k = 0; k < n; ++k) { all_rows += hs[k].m_c; all_cols += hs[k].n_c; }
+  for (int k = 0; k < n; ++k) {
+    BatchSys &d = hs[k];
+    const int64_t nnz = sys[k]->nnz;
+    if (!d.warp_fwd && d.m_c > 0) {
+      d.rpl_fwd = chunk_rows_per_lane(nnz, d.m_c, all_rows);
+      tf[k + 1] = (uint64_t)div_up(d.m_c, (int64_t)kStreamThreads * d.rpl_fwd);
+    }
+    if (!d.warp_bwd && d.n_c > 0) {
+      d.rpl_bwd = chunk_rows_per_lane(nnz, d.n_c, all_cols);
+      tb[k + 1] = (uint64_t)div_up(d.n_c, (int64_t)kStreamThreads * d.rpl_bwd);
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    tf[k + 1] += tf[k];
+    tb[k + 1] += tb[k];
   }
   if (tf[n] >= (1ull << 31) || tb[n] >= (1ull << 31)) { set_error("too many tiles for one launch"); return fail(MC_EINVAL); }
   DevBuf d_cs, d_nv, d_nc;

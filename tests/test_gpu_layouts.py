@@ -226,21 +226,22 @@ def test_mlem_on_a_system_of_the_128_cubed_size_class(mc):
     sysm.free()
 
 
-@pytest.fixture(scope="module")
-def short_rows_ragged(mc):
-    # short rows and columns (the default streaming layout: one lane per
-    # segment, 32 segments per warp, entries read in windows of 128) with the
+@pytest.fixture(scope="module", params=[0.5, 0.2])
+def short_rows_ragged(mc, request):
+    # short rows and columns (the default streaming layout: warp chunks of
+    # 32 R segments, R per lane, entries read in windows of 128) with the
     # awkward cases spelled out: 5013 rows and 3001 columns (the last chunk
-    # of either is partial), half the rows empty and a run of 96 empty rows
-    # (whole empty chunks), one row of 700 entries (several windows), two
-    # rows of 150 entries at a chunk boundary (a window boundary inside a
-    # row), a column of 600 entries and a run of empty columns
+    # of either is partial), half (or 80 %) of the rows empty -- rows of
+    # ~1.8 (~0.9) entries on average, so that a lane takes 2 (4) rows -- and
+    # a run of 512 empty rows (whole empty chunks), one row of 700 entries
+    # (several windows), two adjacent rows of 150 entries (window boundaries
+    # inside rows), a column of 600 entries and a run of empty columns
     n_rows, n_cols = 5013, 3001
-    rows, cols = P.random_events(n_rows, n_cols, (0, 6), 3, seed=51, rows_used=0.5)
-    keep = ~((rows >= 1000) & (rows < 1096)) & ~((cols >= 2000) & (cols < 2100))
+    rows, cols = P.random_events(n_rows, n_cols, (0, 6), 3, seed=51, rows_used=request.param)
+    keep = ~((rows >= 1000) & (rows < 1512)) & ~((cols >= 2000) & (cols < 2100))
     rows, cols = rows[keep], cols[keep]
     rng = np.random.Generator(np.random.Philox(52))
-    outside = np.setdiff1d(np.arange(n_rows), np.arange(1000, 1096))
+    outside = np.setdiff1d(np.arange(n_rows), np.arange(1000, 1512))
     extra_r = [np.full(700, 77), np.full(150, 2015), np.full(150, 2016), rng.choice(outside, 600, replace=False),
                np.array([n_rows - 1])]
     extra_c = [rng.choice(2000, 700, replace=False), rng.choice(2000, 150, replace=False),
@@ -255,7 +256,7 @@ def test_short_segment_layout_edge_cases_match_oracle(mc, short_rows_ragged):
     case = short_rows_ragged
     inf = case.sysm.info()
     assert inf["spmv_fwd"] == 0 and inf["spmv_bwd"] == 0
-    assert case.c.nnz / case.n_rows < 16 and case.c.nnz / case.n_cols < 16   # one lane per segment
+    assert case.c.nnz / case.n_rows < 16 and case.c.nnz / case.n_cols < 16   # warp chunks (not tiles)
     a = case.a.tocsr()
     x = np.linspace(0.5, 2.0, case.n_cols)
     xd = torch.as_tensor(x.astype(np.float32)).cuda()
