@@ -284,10 +284,11 @@ MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t 
 
 /* Projector kernels of a system: fwd (forward projection, CSR) and bwd
  * (back-projection, CSC) each 0 = streaming layout (entries of runs of whole
- * rows staged in shared memory, then one fixed-order sum per row: one lane
- * per row in warps of 32 rows when rows average fewer than 16 entries, else
- * one warp per row in tiles of ~4096 entries), 1, 2, 4, 8, 16 or 32 = that
- * many lanes per row (column), or -1 = keep.  Every layout gives the same
+ * rows staged in shared memory, then one fixed-order sum per row: warps of
+ * 32 R rows, R = 1, 2 or 4 rows per lane, when rows average fewer than 16
+ * entries, else one warp per row in tiles of ~4096 entries), 1, 2, 4, 8,
+ * 16 or 32 = that many lanes per row (column), or -1 = keep.  Every layout
+ * gives the same
  * sums up to FP32 rounding order.  The streaming layout needs every row
  * (column) shorter than 2048 entries: MC_EINVAL otherwise (the system is
  * left unchanged).  Synchronises `stream`. */
