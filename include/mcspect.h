@@ -288,10 +288,9 @@ MC_API int mc_system_set_value_type(mc_system *sys, int32_t value_type, int32_t 
  * 32 R rows, R = 1, 2 or 4 rows per lane, when rows average fewer than 16
  * entries, else one warp per row in tiles of ~4096 entries), 1, 2, 4, 8,
  * 16 or 32 = that many lanes per row (column), or -1 = keep.  Every layout
- * gives the same
- * sums up to FP32 rounding order.  The streaming layout needs every row
- * (column) shorter than 2048 entries: MC_EINVAL otherwise (the system is
- * left unchanged).  Synchronises `stream`. */
+ * gives the same sums up to FP32 rounding order.  The streaming layout needs
+ * every row (column) shorter than 2048 entries: MC_EINVAL otherwise (the
+ * system is left unchanged).  Synchronises `stream`. */
 MC_API int mc_system_set_spmv_layout(mc_system *sys, int32_t fwd, int32_t bwd, void *stream);
 
 /* Forward projection q = A x (Eq. (IMC)): x_dev[N], q_dev[M], float. */
