@@ -433,10 +433,9 @@ MC_API int mc_batch_free(mc_batch *batch);
  * n_cols at most 2^21 each (2,097,152) and at most 4096 log-likelihood
  * values per call; larger requests return MC_EINVAL with a message.  The
  * first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture.  All calls on
- * a device share the array and leave their values in it: calls that overlap
- * on the GPU (other streams, other threads) race and must be serialised by
- * the caller.  The current device must be the one the system was built on
+ * allocation).  All calls on a device share the array and leave their values
+ * in it: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  The current device must be the one the system was built on
  * (MC_EINVAL otherwise: the array is per device).  Results equal
  * mlem_iterate's on the same inputs. */
 MC_API int mlem_iterate_noalloc(const mc_system *sys, const float *y_dev, float *x_dev, int32_t n_iter,
