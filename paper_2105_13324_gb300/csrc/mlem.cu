@@ -498,28 +498,32 @@ __device__ __forceinline__ void chunk_segments(const uint32_t *__restrict__ ptr,
   const uint32_t p0 = __shfl_sync(0xffffffffu, b[0], 0), p1 = __shfl_sync(0xffffffffu, e[R - 1], 31);
   for (uint32_t w0 = p0; w0 < p1; w0 += kChunkWindow) {
     const uint32_t n = min((uint32_t)kChunkWindow, p1 - w0);
+    const uint32_t *ip = idx + w0 + lane;
+    const V *vp = val + w0 + lane;
     uint32_t c[kChunkWindow / 32];
     float v[kChunkWindow / 32];
 #pragma unroll
     for (int u = 0; u < kChunkWindow / 32; ++u) {
-      const uint32_t k = lane + 32u * u;
       c[u] = 0u;
       v[u] = 0.0f;
-      if (k < n) {
-        c[u] = __ldcs(idx + w0 + k);
-        v[u] = to_f(__ldcs(val + w0 + k));
+      if (lane + 32u * u < n) {
+        c[u] = __ldcs(ip + 32 * u);
+        v[u] = to_f(__ldcs(vp + 32 * u));
       }
     }
 #pragma unroll
-    for (int u = 0; u < kChunkWindow / 32; ++u) {
-      const uint32_t k = lane + 32u * u;
-      if (k < n) s_w[k] = v[u] * __ldg(vec + c[u]);
-    }
+    for (int u = 0; u < kChunkWindow / 32; ++u)
+      if (lane + 32u * u < n) s_w[lane + 32 * u] = v[u] * __ldg(vec + c[u]);
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t lo = b[r] > w0 ? b[r] : w0, hi = e[r] < w0 + n ? e[r] : w0 + n;
-      for (uint32_t k = lo; k < hi; ++k) acc[r] += s_w[k - w0];
+      const uint32_t len = hi > lo ? hi - lo : 0u;
+      const float *q = s_w + (len ? lo - w0 : 0u), *qe = q + len;
+      float t = acc[r];
+      for (; q + 1 < qe; q += 2) { t += q[0]; t += q[1]; }
+      if (q < qe) t += q[0];
+      acc[r] = t;
     }
     __syncwarp();
   }
