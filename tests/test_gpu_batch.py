@@ -124,3 +124,42 @@ def test_batch_after_autotune_and_of_a_forced_detection_system(batch_env):
         assert _rel_l2(x.cpu().numpy(), wi) <= MLEM_TOL
     b.free()
     s_fd.free()
+
+
+def test_batch_with_four_rows_per_lane_equals_oracle_mlem(batch_env):
+    # three systems whose non-empty rows and columns average ~1.2 entries,
+    # together large enough for the batch's warp chunks to give each lane 4
+    # rows (columns); graph and cooperative forms against oracle.mlem
+    import torch
+    mc = batch_env[0]
+    n_rows, n_cols = 700_001, 650_003
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    systems, ys, cases = [], [], []
+    m_all = n_all = 0
+    for k in range(3):
+        rows, cols = P.uniform_events(n_rows, n_cols, 300_000, seed=71 + k)
+        c = oracle.system_counts(rows, cols, n_rows, n_cols)
+        H = 2 * n_cols + 1000 * k
+        a = oracle.system_matrix(c, oracle.histories_per_voxel(n_cols, 0, H))
+        y = P.poisson_counts(a @ np.ones(n_cols), 2e5, 81 + k)
+        m_c = int(np.count_nonzero(np.diff(c.tocsr().indptr)))
+        n_c = int(np.count_nonzero(np.diff(c.tocsc().indptr)))
+        assert c.nnz < 1.5 * m_c and c.nnz < 1.5 * n_c
+        m_all, n_all = m_all + m_c, n_all + n_c
+        systems.append(mc.mc_system_from_events(n_rows, n_cols, rows, cols, 0, H))
+        ys.append(torch.as_tensor(y).cuda())
+        cases.append((a, y))
+    assert m_all // 128 >= 32 * sm and n_all // 128 >= 32 * sm   # 4 rows per lane
+    xs = [torch.zeros(n_cols, device="cuda") for _ in systems]
+    b = mc.Batch(systems, ys, xs)
+    want = _oracle_images(cases, 15)
+    for run in (b.mlem, b.mlem_persistent):
+        run(15)
+        torch.cuda.synchronize()
+        for x, w in zip(xs, want):
+            got = x.cpu().numpy().astype(np.float64)
+            assert _rel_l2(got, w) <= MLEM_TOL
+            np.testing.assert_allclose(got, w, rtol=1e-4, atol=1e-6 * float(w.max()))
+    b.free()
+    for s in systems:
+        s.free()

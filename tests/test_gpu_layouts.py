@@ -232,8 +232,9 @@ def short_rows_ragged(mc, request):
     # 32 R segments, R per lane, entries read in windows of 128) with the
     # awkward cases spelled out: 5013 rows and 3001 columns (the last chunk
     # of either is partial), half (or 80 %) of the rows empty -- rows of
-    # ~1.8 (~0.9) entries on average, so that a lane takes 2 (4) rows -- and
-    # a run of 512 empty rows (whole empty chunks), one row of 700 entries
+    # ~1.8 (~0.9) entries on average; the launch is too small for more than
+    # one row per lane, which the larger cases below cover -- and a run of
+    # 512 empty rows (whole empty chunks), one row of 700 entries
     # (several windows), two adjacent rows of 150 entries (window boundaries
     # inside rows), a column of 600 entries and a run of empty columns
     n_rows, n_cols = 5013, 3001
@@ -283,3 +284,47 @@ def test_short_segment_layout_edge_cases_match_oracle(mc, short_rows_ragged):
         case.sysm.set_value_type(vt)
         _check_image(case.gpu_image(mc), case.oracle_image(case.a))
     case.sysm.set_value_type("f32")
+
+
+def _rows_per_lane(nnz, n, launch_segments, sm_count):
+    """Rows (columns) per lane that the streaming layout's warp chunks take
+    for n segments averaging nnz / n entries in a launch of launch_segments
+    segments, restated from the library so that a test can state which
+    kernel its case runs."""
+    r = 1 if nnz >= 3 * n else 2 if nnz >= 1.5 * n else 4
+    while r > 1 and launch_segments // (32 * r) < sm_count * 32:
+        r //= 2
+    return r
+
+
+@pytest.mark.parametrize("n_rows,n_cols,n_events,want", [(330_007, 320_009, 640_000, 2),
+                                                         (700_001, 650_003, 620_000, 4)])
+def test_rows_per_lane_kernels_match_oracle(mc, n_rows, n_cols, n_events, want):
+    # systems large enough for the warp chunks to give each lane 2 (4) rows
+    # and columns; every projector and ML-EM against the oracle
+    import torch
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    rows, cols = P.uniform_events(n_rows, n_cols, n_events, seed=61 + want)
+    case = _Case(mc, n_rows, n_cols, rows, cols, 3 * n_cols + 7, seed=62 + want)
+    nnz = case.c.nnz
+    assert _rows_per_lane(nnz, n_rows, n_rows, sm) == want and _rows_per_lane(nnz, n_cols, n_cols, sm) == want
+    inf = case.sysm.info()
+    assert inf["spmv_fwd"] == 0 and inf["spmv_bwd"] == 0
+    a = case.a.tocsr()
+    x = np.linspace(0.5, 2.0, n_cols)
+    xd = torch.as_tensor(x.astype(np.float32)).cuda()
+    q = torch.zeros(n_rows, dtype=torch.float32, device="cuda")
+    mc.mc_project(case.sysm, xd, q)
+    q_want = a @ x.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(q.cpu().numpy(), q_want, rtol=1e-6, atol=1e-7 * q_want.max())
+    r = np.linspace(0.0, 3.0, n_rows)
+    b = torch.zeros(n_cols, dtype=torch.float32, device="cuda")
+    mc.mc_backproject(case.sysm, torch.as_tensor(r.astype(np.float32)).cuda(), b)
+    b_want = a.T @ r.astype(np.float32).astype(np.float64)
+    np.testing.assert_allclose(b.cpu().numpy(), b_want, rtol=1e-6, atol=1e-7 * b_want.max())
+    ll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mc.mc_loglik(case.sysm, xd, case.yd, ll)
+    ll_want = oracle.loglik(a, x.astype(np.float32), case.y)
+    assert abs(float(ll[0]) - ll_want) <= 1e-6 * abs(ll_want)
+    _check_image(case.gpu_image(mc), case.oracle_image(case.a))
+    case.sysm.free()
