@@ -403,8 +403,11 @@ MC_API int mc_system_autotune(mc_system *sys, void *stream);
  * (mc_mlem_init) and runs n_iter updates of Eq. (MLEM) for all of them: one
  * forward and one back-projection launch per iteration over all systems,
  * captured once into a CUDA graph per n_iter and replayed.  Every system
- * must be a full FP32 system with the streaming layout (short rows, as MC
- * matrices of moderate history counts have); results equal mlem_iterate's.
+ * must be a full (not ordered-subset) FP32 system, of any projector layout:
+ * the batch makes its own work units over each system's non-empty rows and
+ * columns (warp chunks; tiles of one warp per row where rows or columns
+ * average 16 or more entries, which then must be shorter than 2048 entries,
+ * else MC_EINVAL).  Results equal mlem_iterate's up to FP32 rounding order.
  * Systems in a batch must not be used by other calls while it runs. */
 typedef struct mc_batch mc_batch;
 MC_API int mc_batch_create(mc_system *const *systems, int32_t n, const float *const *y_dev, float *const *x_dev,
