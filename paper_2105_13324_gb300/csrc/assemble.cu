@@ -463,17 +463,259 @@ static int bits_for(uint64_t range) {
   return b;
 }
 
-int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, const uint64_t *weights) {
-  const uint64_t M = (uint64_t)sys->n_rows, N = (uint64_t)sys->n_cols;
-  // n_v and 1/n_v
-  MCS_TRY(sys->n_v.alloc(N * sizeof(uint32_t), s));
-  MCS_TRY(sys->inv_n.alloc(N * sizeof(float), s));
-  count_launch(); histories_per_voxel_kernel<<<grid_for((int64_t)N), 256, 0, s>>>(sys->first, sys->count, N, sys->n_v.as<uint32_t>(),
-                                                                   sys->inv_n.as<float>());
-  MCS_LAUNCHED();
+// ---------------------------------------------------------------------------
+// assembly by buckets (unweighted events, short columns and rows)
+// ---------------------------------------------------------------------------
+// Events are counted per column and each event's row is placed in its
+// column's bucket (in any order); every bucket is then sorted by row, one
+// thread per bucket, with equal rows merged into a count.  The CSR is made
+// the same way from the CSC entries.  Sorting makes the result unique: the
+// same sorted, merged CSC and CSR as the radix path, in a few passes over
+// the events instead of one per digit.  Taken only when no column holds more
+// than kBucketLen events and no row more than kBucketLen entries.
+constexpr int kBucketLen = 64;
 
+__global__ void bucket_count_kernel(const uint64_t *keys, int64_t n, uint64_t m, uint32_t *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[keys[i] / m], 1u);
+}
+
+// event i -> its row, at start[column] + (its place among the column's
+// events, in arrival order at the atomic)
+__global__ void bucket_fill_kernel(const uint64_t *keys, int64_t n, uint64_t m, const uint32_t *start,
+                                   uint32_t *cursor, uint32_t *minor) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const uint64_t v = k / m;
+    minor[start[v] + atomicAdd(&cursor[v], 1u)] = (uint32_t)(k - v * m);
+  }
+}
+
+// Compare-exchange of (a[i], w[i]) and (a[k], w[k]) by a.
+__device__ __forceinline__ void cmp_swap(uint32_t &ai, uint32_t &wi, uint32_t &ak, uint32_t &wk) {
+  if (ak < ai) {
+    const uint32_t t = ai, u = wi;
+    ai = ak; wi = wk;
+    ak = t; wk = u;
+  }
+}
+
+// Sort bucket c = [start[c], start[c + 1]) of `minor` ascending, with its
+// payload (cnt_in, or 1 per element when cnt_in is NULL), merge equal
+// values (payloads summed) and write the u merged values and payloads to
+// the bucket's first u places of minor and cnt_out; uniq[c] = u.  Buckets of
+// up to 8 elements are sorted in registers (Batcher's odd-even merge
+// network, unused places holding the largest value); longer ones, up to
+// kBucketLen, by insertion in a local array.  A longer bucket sets
+// *overflow and is left as it is.
+__global__ void bucket_sort_merge_kernel(const uint32_t *start, int64_t n_major, uint32_t *minor,
+                                         const uint32_t *cnt_in, uint32_t *cnt_out, uint32_t *uniq,
+                                         unsigned int *overflow) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_major;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = start[c];
+    const int len = (int)(start[c + 1] - b);
+    if (len > kBucketLen) {
+      atomicOr(overflow, 1u);
+      continue;
+    }
+    if (len <= 8) {
+      uint32_t r[8], q[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        r[k] = k < len ? minor[b + k] : 0xffffffffu;
+        q[k] = k < len ? (cnt_in ? cnt_in[b + k] : 1u) : 0u;
+      }
+      // odd-even merge sort of 8: sorted pairs, fours, then eight
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) cmp_swap(r[k], q[k], r[k + 1], q[k + 1]);
+#pragma unroll
+      for (int k = 0; k < 8; k += 4) {
+        cmp_swap(r[k], q[k], r[k + 2], q[k + 2]);
+        cmp_swap(r[k + 1], q[k + 1], r[k + 3], q[k + 3]);
+        cmp_swap(r[k + 1], q[k + 1], r[k + 2], q[k + 2]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cmp_swap(r[k], q[k], r[k + 4], q[k + 4]);
+      cmp_swap(r[2], q[2], r[4], q[4]);
+      cmp_swap(r[3], q[3], r[5], q[5]);
+      cmp_swap(r[1], q[1], r[2], q[2]);
+      cmp_swap(r[3], q[3], r[4], q[4]);
+      cmp_swap(r[5], q[5], r[6], q[6]);
+      // merge equal values and write, all from registers (the loads are done)
+      int u = 0;
+      uint32_t last = 0u, acc = 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k < len) {
+          if (u > 0 && r[k] == last) {
+            acc += q[k];
+          } else {
+            if (u > 0) {
+              minor[b + u - 1] = last;
+              cnt_out[b + u - 1] = acc;
+            }
+            last = r[k];
+            acc = q[k];
+            ++u;
+          }
+        }
+      }
+      if (u > 0) {
+        minor[b + u - 1] = last;
+        cnt_out[b + u - 1] = acc;
+      }
+      uniq[c] = (uint32_t)u;
+      continue;
+    }
+    uint32_t a[kBucketLen], w[kBucketLen];
+    {
+      for (int k = 0; k < len; ++k) {  // insertion sort while loading
+        const uint32_t x = minor[b + k], y = cnt_in ? cnt_in[b + k] : 1u;
+        int t = k;
+        for (; t > 0 && a[t - 1] > x; --t) {
+          a[t] = a[t - 1];
+          w[t] = w[t - 1];
+        }
+        a[t] = x;
+        w[t] = y;
+      }
+    }
+    int u = 0;
+    for (int k = 0; k < len; ++k) {
+      if (u > 0 && a[k] == a[u - 1]) {
+        w[u - 1] += w[k];
+      } else {
+        a[u] = a[k];
+        w[u] = w[k];
+        ++u;
+      }
+    }
+    for (int k = 0; k < u; ++k) {
+      minor[b + k] = a[k];
+      cnt_out[b + k] = w[k];
+    }
+    uniq[c] = (uint32_t)u;
+  }
+}
+
+// CSC: bucket c's merged entries to [col_ptr[c], col_ptr[c + 1]), and the
+// number of entries of each row
+__global__ void bucket_compact_kernel(const uint32_t *start, const uint32_t *col_ptr, int64_t n_cols,
+                                      const uint32_t *minor, const uint32_t *cnt, uint32_t *row_idx,
+                                      uint32_t *csc_cnt, uint32_t *row_hist) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cols;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = start[c], o = col_ptr[c], u = col_ptr[c + 1] - o;
+    for (uint32_t k = 0; k < u; ++k) {
+      const uint32_t j = minor[b + k];
+      row_idx[o + k] = j;
+      csc_cnt[o + k] = cnt[b + k];
+      atomicAdd(&row_hist[j], 1u);
+    }
+  }
+}
+
+// CSR buckets: every CSC entry (j, v) to row j's bucket (any order)
+__global__ void transpose_fill_kernel(const uint32_t *col_ptr, int64_t n_cols, const uint32_t *row_idx,
+                                      const uint32_t *csc_cnt, const uint32_t *row_ptr, uint32_t *cursor,
+                                      uint32_t *col_idx, uint32_t *csr_cnt) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cols;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    for (uint32_t k = col_ptr[c]; k < col_ptr[c + 1]; ++k) {
+      const uint32_t j = row_idx[k];
+      const uint32_t pos = row_ptr[j] + atomicAdd(&cursor[j], 1u);
+      col_idx[pos] = (uint32_t)c;
+      csr_cnt[pos] = csc_cnt[k];
+    }
+  }
+}
+
+// The CSC and CSR of n > 0 unweighted events by buckets.  Sets *done, or
+// leaves the system's matrix unfinished (and the keys untouched) when a
+// column or a row is too long for a bucket.
+static int assemble_buckets(mc_system *sys, const uint64_t *keys, int64_t n, cudaStream_t s, bool *done) {
+  *done = false;
+  const int64_t M = sys->n_rows, N = sys->n_cols;
+  DevBuf ccnt, start, flag;
+  MCS_TRY(ccnt.alloc((size_t)(N + 1) * sizeof(uint32_t), s));
+  MCS_TRY(start.alloc((size_t)(N + 1) * sizeof(uint32_t), s));
+  MCS_TRY(flag.alloc(sizeof(unsigned int), s));
+  MCS_CUDA(cudaMemsetAsync(ccnt.p, 0, (size_t)(N + 1) * sizeof(uint32_t), s));
+  MCS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(unsigned int), s));
+  count_launch(); bucket_count_kernel<<<grid_for(n), 256, 0, s>>>(keys, n, (uint64_t)M, ccnt.as<uint32_t>());
+  MCS_LAUNCHED();
+  MCS_TRY(exclusive_scan_u32(ccnt.as<uint32_t>(), start.as<uint32_t>(), N + 1, s));
+  // events into column buckets, sorted and merged
+  DevBuf minor, ecnt;
+  MCS_TRY(minor.alloc((size_t)n * sizeof(uint32_t), s));
+  MCS_TRY(ecnt.alloc((size_t)n * sizeof(uint32_t), s));
+  MCS_CUDA(cudaMemsetAsync(ccnt.p, 0, (size_t)(N + 1) * sizeof(uint32_t), s));  // now the bucket cursors
+  count_launch();
+  bucket_fill_kernel<<<grid_for(n), 256, 0, s>>>(keys, n, (uint64_t)M, start.as<uint32_t>(), ccnt.as<uint32_t>(),
+                                                 minor.as<uint32_t>());
+  MCS_LAUNCHED();
+  // ccnt becomes the merged entries per column (ccnt[N] stays 0 for the scan)
+  count_launch();
+  bucket_sort_merge_kernel<<<grid_for(N), 256, 0, s>>>(start.as<uint32_t>(), N, minor.as<uint32_t>(), nullptr,
+                                                       ecnt.as<uint32_t>(), ccnt.as<uint32_t>(),
+                                                       flag.as<unsigned int>());
+  MCS_LAUNCHED();
+  MCS_TRY(sys->col_ptr.alloc((size_t)(N + 1) * sizeof(uint32_t), s));
+  MCS_TRY(exclusive_scan_u32(ccnt.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), N + 1, s));
+  uint32_t nnz = 0, too_long = 0;
+  MCS_CUDA(cudaMemcpyAsync(&nnz, sys->col_ptr.as<uint32_t>() + N, sizeof(nnz), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaMemcpyAsync(&too_long, flag.p, sizeof(too_long), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  if (too_long) return MC_OK;  // a column of more than kBucketLen events
+  const size_t nnz_b = (size_t)(nnz > 0 ? nnz : 1);
+  MCS_TRY(sys->row_idx.alloc(nnz_b * sizeof(uint32_t), s));
+  MCS_TRY(sys->csc_cnt.alloc(nnz_b * sizeof(uint32_t), s));
+  DevBuf rhist;
+  MCS_TRY(rhist.alloc((size_t)(M + 1) * sizeof(uint32_t), s));
+  MCS_CUDA(cudaMemsetAsync(rhist.p, 0, (size_t)(M + 1) * sizeof(uint32_t), s));
+  count_launch();
+  bucket_compact_kernel<<<grid_for(N), 256, 0, s>>>(start.as<uint32_t>(), sys->col_ptr.as<uint32_t>(), N,
+                                                    minor.as<uint32_t>(), ecnt.as<uint32_t>(),
+                                                    sys->row_idx.as<uint32_t>(), sys->csc_cnt.as<uint32_t>(),
+                                                    rhist.as<uint32_t>());
+  MCS_LAUNCHED();
+  minor.release();
+  ecnt.release();
+  start.release();
+  ccnt.release();
+  // CSR: the CSC entries into row buckets, each sorted by column
+  MCS_TRY(sys->row_ptr.alloc((size_t)(M + 1) * sizeof(uint32_t), s));
+  MCS_TRY(exclusive_scan_u32(rhist.as<uint32_t>(), sys->row_ptr.as<uint32_t>(), M + 1, s));
+  MCS_TRY(sys->col_idx.alloc(nnz_b * sizeof(uint32_t), s));
+  MCS_TRY(sys->csr_cnt.alloc(nnz_b * sizeof(uint32_t), s));
+  MCS_CUDA(cudaMemsetAsync(rhist.p, 0, (size_t)(M + 1) * sizeof(uint32_t), s));  // the row cursors
+  count_launch();
+  transpose_fill_kernel<<<grid_for(N), 256, 0, s>>>(sys->col_ptr.as<uint32_t>(), N, sys->row_idx.as<uint32_t>(),
+                                                    sys->csc_cnt.as<uint32_t>(), sys->row_ptr.as<uint32_t>(),
+                                                    rhist.as<uint32_t>(), sys->col_idx.as<uint32_t>(),
+                                                    sys->csr_cnt.as<uint32_t>());
+  MCS_LAUNCHED();
+  // rows hold distinct columns: the sort leaves every entry (rhist takes the
+  // per-row counts, unused)
+  count_launch();
+  bucket_sort_merge_kernel<<<grid_for(M), 256, 0, s>>>(sys->row_ptr.as<uint32_t>(), M, sys->col_idx.as<uint32_t>(),
+                                                       sys->csr_cnt.as<uint32_t>(), sys->csr_cnt.as<uint32_t>(),
+                                                       rhist.as<uint32_t>(), flag.as<unsigned int>());
+  MCS_LAUNCHED();
+  MCS_CUDA(cudaMemcpyAsync(&too_long, flag.p, sizeof(too_long), cudaMemcpyDeviceToHost, s));
+  MCS_CUDA(cudaStreamSynchronize(s));
+  if (too_long) return MC_OK;  // a row of more than kBucketLen entries
+  sys->nnz = nnz;
+  *done = true;
+  return MC_OK;
+}
+
+// Steps 1-4 of the assembly by a radix sort of the event keys (any events,
+// weighted or not).
+static int assemble_radix(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, const uint64_t *weights) {
+  const uint64_t M = (uint64_t)sys->n_rows, N = (uint64_t)sys->n_cols;
   // 1. sort events by (v, j); weighted: with the event index as payload
-  sys->weighted = weights != nullptr;
   DevBuf alt, perm, perm_alt, went;
   MCS_TRY(alt.alloc((size_t)(n > 0 ? n : 1) * sizeof(uint64_t), s));
   if (weights) {
@@ -594,6 +836,26 @@ int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, con
   }
   tkeys.release();
   went.release();
+
+  return MC_OK;
+}
+
+int assemble_system(mc_system *sys, DevBuf &keys, int64_t n, cudaStream_t s, const uint64_t *weights) {
+  const uint64_t N = (uint64_t)sys->n_cols;
+  // n_v and 1/n_v
+  MCS_TRY(sys->n_v.alloc(N * sizeof(uint32_t), s));
+  MCS_TRY(sys->inv_n.alloc(N * sizeof(float), s));
+  count_launch(); histories_per_voxel_kernel<<<grid_for((int64_t)N), 256, 0, s>>>(sys->first, sys->count, N, sys->n_v.as<uint32_t>(),
+                                                                   sys->inv_n.as<float>());
+  MCS_LAUNCHED();
+  sys->weighted = weights != nullptr;
+
+  // 1-4. the CSC and CSR: by buckets where columns and rows are short, else
+  // by a radix sort
+  bool bucketed = false;
+  if (!weights && n > 0 && n < ((int64_t)1 << 31)) MCS_TRY(assemble_buckets(sys, keys.as<uint64_t>(), n, s, &bucketed));
+  if (bucketed) keys.release();
+  else MCS_TRY(assemble_radix(sys, keys, n, s, weights));
 
   // 5. column sums S_v and the largest count
   {

@@ -263,6 +263,65 @@ def test_assembly_from_events_is_bit_exact(mc, n_rows, n_cols, n_events, seed):
     assert info["max_count"] == (int(want.data.max()) if want.nnz else 0)
 
 
+def _bucket_case(kind):
+    """Events for the assembly cases below: (n_rows, n_cols, rows, cols)."""
+    rng = np.random.Generator(np.random.Philox(100 + len(kind)))
+    if kind in ("uniform", "uniform_large"):
+        n_rows, n_cols, n = (5003, 3001, 20_011) if kind == "uniform" else (300_007, 200_003, 1_000_003)
+        rows = rng.integers(0, n_rows, n)
+        cols = rng.integers(0, n_cols, n)
+        dup = rng.choice(n, n // 10, replace=False)          # repeated events: counts above 1
+        rows, cols = np.concatenate([rows, rows[dup], rows[dup[:n // 50]]]), np.concatenate([cols, cols[dup], cols[dup[:n // 50]]])
+    elif kind in ("column_of_64", "column_of_65"):
+        n_rows, n_cols = 4001, 2003
+        rows = rng.integers(0, n_rows, 8000)
+        cols = rng.integers(0, n_cols, 8000)
+        cols[cols == 17] = 18
+        extra = 64 if kind == "column_of_64" else 65
+        rows = np.concatenate([rows, rng.choice(n_rows, extra, replace=False)])
+        cols = np.concatenate([cols, np.full(extra, 17)])
+    else:  # one long row over short columns
+        n_rows, n_cols = 4001, 2003
+        rows = np.concatenate([rng.integers(0, n_rows, 8000), np.full(300, 11)])
+        cols = np.concatenate([rng.integers(0, n_cols, 8000), rng.choice(n_cols, 300, replace=False)])
+    return n_rows, n_cols, rows.astype(np.int32), cols.astype(np.int32)
+
+
+@pytest.mark.parametrize("kind,buckets", [("uniform", True), ("uniform_large", True), ("column_of_64", True),
+                                          ("column_of_65", False), ("long_row", False)])
+def test_assembly_by_buckets_and_its_fallbacks_is_bit_exact(mc, kind, buckets):
+    # unweighted events whose columns hold at most 64 events and rows at
+    # most 64 entries are assembled by column and row buckets; a longer
+    # column, or a longer row found after the CSC was made, falls back to the
+    # radix sort.  Every case equals the oracle's matrix exactly.
+    n_rows, n_cols, rows, cols = _bucket_case(kind)
+    want = oracle.system_counts(rows, cols, n_rows, n_cols)
+    longest_col = int(np.bincount(cols, minlength=n_cols).max())
+    longest_row = int(np.diff(sp.csr_matrix(want).indptr).max())
+    assert (longest_col <= 64 and longest_row <= 64) == buckets
+    H = 7 * n_cols + 5
+    sysm = mc.mc_system_from_events(n_rows, n_cols, rows, cols, 0, H)
+    cp, ri, cnt, nv = sysm.export_csc()
+    np.testing.assert_array_equal(cp, want.indptr)
+    np.testing.assert_array_equal(ri, want.indices)
+    np.testing.assert_array_equal(cnt, want.data)
+    np.testing.assert_array_equal(nv, oracle.histories_per_voxel(n_cols, 0, H))
+    rp, ci, cr = sysm.export_csr()
+    wr = sp.csr_matrix(want)
+    wr.sort_indices()
+    np.testing.assert_array_equal(rp, wr.indptr)
+    np.testing.assert_array_equal(ci, wr.indices)
+    np.testing.assert_array_equal(cr, wr.data)
+    info = sysm.info()
+    assert info["nnz"] == want.nnz and info["n_events"] == len(rows)
+    assert info["max_count"] == int(want.data.max())
+    import torch
+    s = torch.zeros(n_cols, dtype=torch.float64, device="cuda")
+    mc.mc_sensitivity(sysm, s)
+    np.testing.assert_allclose(s.cpu().numpy(), oracle.sensitivity(oracle.system_matrix(want, nv)), rtol=1e-13)
+    sysm.free()
+
+
 # ---------------------------------------------------------------------------
 # projectors and ML-EM (oracle matrix uploaded as events)
 # ---------------------------------------------------------------------------
