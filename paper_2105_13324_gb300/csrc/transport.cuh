@@ -398,6 +398,17 @@ __device__ __forceinline__ void push_event(const EventSink &s, unsigned long lon
   }
 }
 
+// The acceptance-cone test of try_view alone: view k can accept a photon
+// moving along d (no draw).
+template <typename T>
+__device__ __forceinline__ bool in_cone(const TArgs<T> &a, int k, T dx, T dy) {
+  const T ck = a.view_cs[2 * k], sk = a.view_cs[2 * k + 1];
+  const T c = dx * ck + dy * sk;
+  if (!(c > (T)0)) return false;
+  const T stt = sqrt0<T>((T)1 - c * c);
+  return a.ratio * stt < c;
+}
+
 // Offer view k to an escaping photon at p (inside the grid) moving along d.
 template <typename T, bool TRACE>
 __device__ __forceinline__ void try_view(const TArgs<T> &a, KStream &st, int k, T px, T py, T pz, T dx, T dy,
@@ -445,7 +456,11 @@ __device__ __forceinline__ int floor_div(int a, int b) {
 // azimuth window when the views tile the full turn evenly.  The window is
 // wider than the acceptance cone (a candidate needs |azimuth - theta_k| below
 // the cone's half-angle), so exactly the same views are tested as in a plain
-// loop, in the same order.
+// loop, in the same order.  The window's views are cone-tested first and the
+// candidates then offered in order: each lane has one or two candidates
+// among ~5 window views, so the expensive part of try_view runs once per
+// candidate place of the warp instead of once per window view, with more
+// lanes taking part each time.
 template <typename T, bool TRACE>
 __device__ __forceinline__ void detect(const TArgs<T> &a, KStream &st, T px, T py, T pz, T dx, T dy, T dz,
                                        uint32_t v, const EventSink &sink) {
@@ -459,10 +474,35 @@ __device__ __forceinline__ void detect(const TArgs<T> &a, KStream &st, T px, T p
       const int sh = floor_div(kmin, K) * K;
       kmin -= sh;
       kmax -= sh;
+      const int hi = kmax < K - 1 ? kmax : K - 1;
+      // 1. the window's candidate views -- the cone test alone, no draws --
+      // in ascending order, 8 bits each
+      uint64_t list = 0ull;
+      int nc = 0;
+      bool full = false;
+      auto consider = [&](int k) {
+        if (in_cone<T>(a, k, dx, dy)) {
+          if (nc < 8 && k < 256) {
+            list |= (uint64_t)k << (8 * nc);
+            ++nc;
+          } else {
+            full = true;
+          }
+        }
+      };
+      if (kmax >= K)
+        for (int k = 0; k <= kmax - K && k < a.n_views; ++k) consider(k);
+      for (int k = kmin; k <= hi && k < a.n_views; ++k) consider(k);
+      if (!full) {
+        // 2. the candidates in order with their draws: a warp runs this
+        // once per candidate place rather than once per window view
+        for (int t = 0; t < nc; ++t)
+          try_view<T, TRACE>(a, st, (int)((list >> (8 * t)) & 255u), px, py, pz, dx, dy, dz, v, sink);
+        return;
+      }
       if (kmax >= K) {
         for (int k = 0; k <= kmax - K && k < a.n_views; ++k) try_view<T, TRACE>(a, st, k, px, py, pz, dx, dy, dz, v, sink);
       }
-      const int hi = kmax < K - 1 ? kmax : K - 1;
       for (int k = kmin; k <= hi && k < a.n_views; ++k) try_view<T, TRACE>(a, st, k, px, py, pz, dx, dy, dz, v, sink);
       return;
     }
