@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
                                                                    const uint32_t *__restrict__ rmap,
                                                                    const float *__restrict__ add) {
   __shared__ double s_tmp[kSpmvThreads / 32];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t gid = ((int64_t)blockIdx.x * kSpmvThreads + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
   double ll = 0.0;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(kSpmvThreads) csc_back_kernel(const uint32_t *
                                                                 const float *__restrict__ inv_n,
                                                                 const float *__restrict__ inv_colsum,
                                                                 float *__restrict__ x, float *__restrict__ xs) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int64_t gid = ((int64_t)blockIdx.x * kSpmvThreads + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
   uint32_t b = 0, e = 0;
@@ -550,6 +552,7 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_forward_kernel(const uint
                                                                    const float *__restrict__ add) {
   __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
   __shared__ double s_tmp[kChunkThreads / 32];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   FwdOut<MODE, LL> o{y, out, rmap, add, 0.0};
   chunk_segments<R, V>(row_ptr, m, col, val, xs, s_w[threadIdx.x >> 5], o, chunk_first<R>());
   if (LL) {
@@ -567,6 +570,7 @@ __global__ void __launch_bounds__(kChunkThreads) chunk_back_kernel(const uint32_
                                                                 const float *__restrict__ inv_colsum,
                                                                 float *__restrict__ x, float *__restrict__ xs) {
   __shared__ float s_w[kChunkThreads / 32][kChunkWindow];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   BackOut<MODE> o{inv_n, inv_colsum, x, xs};
   chunk_segments<R, V>(col_ptr, n, row, val, r, s_w[threadIdx.x >> 5], o, chunk_first<R>());
 }
@@ -607,6 +611,25 @@ __global__ void tile_bounds_kernel(const uint32_t *ptr, int64_t n, uint32_t step
 // ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
+// Launch with programmatic stream serialisation: the grid may be scheduled
+// while the previous kernel on the stream drains; the projector kernels
+// launched this way wait at griddepcontrol.wait, before any memory access,
+// until that kernel has completed and its writes are visible, so the order
+// of the two is that of a plain launch with the launch latency hidden.
+template <typename... P, typename... A>
+static void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 static int grid_stride_blocks(int64_t n) {
   int64_t g = (n + 255) / 256;
   const int64_t cap = (int64_t)device_sm_count() * 16;
@@ -622,12 +645,12 @@ static void fwd_launch(const mc_system *sys, int g, const float *xs, const float
   const V *val = sys->csr_val.as<V>();
   const uint32_t *rp = sys->row_ptr.as<uint32_t>(), *ci = sys->col_idx.as<uint32_t>();
   switch (g) {
-    case 1: count_launch(); csr_forward_kernel<V, 1, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
-    case 2: count_launch(); csr_forward_kernel<V, 2, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
-    case 4: count_launch(); csr_forward_kernel<V, 4, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
-    case 8: count_launch(); csr_forward_kernel<V, 8, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
-    case 16: count_launch(); csr_forward_kernel<V, 16, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
-    default: count_launch(); csr_forward_kernel<V, 32, MODE, LL><<<blocks, kSpmvThreads, 0, s>>>(rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 1: count_launch(); launch_pdl(csr_forward_kernel<V, 1, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 2: count_launch(); launch_pdl(csr_forward_kernel<V, 2, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 4: count_launch(); launch_pdl(csr_forward_kernel<V, 4, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 8: count_launch(); launch_pdl(csr_forward_kernel<V, 8, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    case 16: count_launch(); launch_pdl(csr_forward_kernel<V, 16, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
+    default: count_launch(); launch_pdl(csr_forward_kernel<V, 32, MODE, LL>, blocks, kSpmvThreads, s, rp, ci, val, xs, m, y, out, partials, rmap, add); break;
   }
 }
 
@@ -639,14 +662,15 @@ static void back_launch(const mc_system *sys, int g, const float *r, float *x, f
   const uint32_t *cp = sys->col_ptr.as<uint32_t>(), *ri = sys->row_idx.as<uint32_t>();
   const float *inv_n = proj_scale(sys), *ics = proj_inv_norm(sys);
   switch (g) {
-    case 1: count_launch(); csc_back_kernel<V, 1, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
-    case 2: count_launch(); csc_back_kernel<V, 2, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
-    case 4: count_launch(); csc_back_kernel<V, 4, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
-    case 8: count_launch(); csc_back_kernel<V, 8, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
-    case 16: count_launch(); csc_back_kernel<V, 16, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
-    default: count_launch(); csc_back_kernel<V, 32, MODE><<<blocks, kSpmvThreads, 0, s>>>(cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    case 1: count_launch(); launch_pdl(csc_back_kernel<V, 1, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    case 2: count_launch(); launch_pdl(csc_back_kernel<V, 2, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    case 4: count_launch(); launch_pdl(csc_back_kernel<V, 4, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    case 8: count_launch(); launch_pdl(csc_back_kernel<V, 8, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    case 16: count_launch(); launch_pdl(csc_back_kernel<V, 16, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
+    default: count_launch(); launch_pdl(csc_back_kernel<V, 32, MODE>, blocks, kSpmvThreads, s, cp, ri, val, r, n, inv_n, ics, x, xs); break;
   }
 }
+
 
 template <typename V, int MODE, bool LL>
 static void stream_fwd_launch(const mc_system *sys, const float *xs, const float *y, float *out, double *partials,
@@ -661,15 +685,10 @@ static void stream_fwd_launch(const mc_system *sys, const float *xs, const float
   else {
     const int R = chunk_rows_per_lane(sys->nnz, sys->n_rows, sys->n_rows);
     const unsigned g = (unsigned)div_up(sys->n_rows, (int64_t)kChunkThreads * R);
-    if (R == 1)
-      chunk_forward_kernel<1, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
-                                                                     rmap, add);
-    else if (R == 2)
-      chunk_forward_kernel<2, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
-                                                                     rmap, add);
-    else
-      chunk_forward_kernel<4, V, MODE, LL><<<g, kChunkThreads, 0, s>>>(rp, sys->n_rows, ci, val, xs, y, out, partials,
-                                                                     rmap, add);
+    const int64_t m = sys->n_rows;
+    if (R == 1) launch_pdl(chunk_forward_kernel<1, V, MODE, LL>, g, kChunkThreads, s, rp, m, ci, val, xs, y, out, partials, rmap, add);
+    else if (R == 2) launch_pdl(chunk_forward_kernel<2, V, MODE, LL>, g, kChunkThreads, s, rp, m, ci, val, xs, y, out, partials, rmap, add);
+    else launch_pdl(chunk_forward_kernel<4, V, MODE, LL>, g, kChunkThreads, s, rp, m, ci, val, xs, y, out, partials, rmap, add);
   }
 }
 
@@ -685,12 +704,10 @@ static void stream_back_launch(const mc_system *sys, const float *r, float *x, f
   else {
     const int R = chunk_rows_per_lane(sys->nnz, sys->n_cols, sys->n_cols);
     const unsigned g = (unsigned)div_up(sys->n_cols, (int64_t)kChunkThreads * R);
-    if (R == 1)
-      chunk_back_kernel<1, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
-    else if (R == 2)
-      chunk_back_kernel<2, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
-    else
-      chunk_back_kernel<4, V, MODE><<<g, kChunkThreads, 0, s>>>(cp, sys->n_cols, ri, val, r, inv_n, ics, x, xs);
+    const int64_t n = sys->n_cols;
+    if (R == 1) launch_pdl(chunk_back_kernel<1, V, MODE>, g, kChunkThreads, s, cp, n, ri, val, r, inv_n, ics, x, xs);
+    else if (R == 2) launch_pdl(chunk_back_kernel<2, V, MODE>, g, kChunkThreads, s, cp, n, ri, val, r, inv_n, ics, x, xs);
+    else launch_pdl(chunk_back_kernel<4, V, MODE>, g, kChunkThreads, s, cp, n, ri, val, r, inv_n, ics, x, xs);
   }
 }
 
