@@ -140,7 +140,12 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
   // every lane takes part in the shuffles; lanes past the last row see an
   // empty range
   uint32_t b = 0, e = 0;
-  if (gid < m) { b = row_ptr[gid]; e = row_ptr[gid + 1]; }
+  float yv = 0.0f;  // the ratio's y, issued ahead of the gathers
+  if (gid < m) {
+    b = row_ptr[gid];
+    e = row_ptr[gid + 1];
+    if (MODE == 1 && sub == 0) yv = y[gid];
+  }
   float acc = segment_dot<V, G>(b, e, col, val, xs, sub);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
@@ -148,11 +153,11 @@ __global__ void __launch_bounds__(kSpmvThreads) csr_forward_kernel(const uint32_
     if (MODE == 0) {
       out[gid] = acc;
     } else {
-      out[gid] = ratio_out<MODE>(acc, gid, y, rmap, add);
+      out[gid] = MODE == 1 ? (acc > 0.0f ? yv / acc : 0.0f) : ratio_out<MODE>(acc, gid, y, rmap, add);
       if (LL) {
         // a bin with an empty row is left out of the y ln q sum (q = 0 for
         // every image: the term carries no information about x)
-        const float yj = y[gid];
+        const float yj = MODE == 1 ? yv : y[gid];
         ll = (yj > 0.0f && e > b ? (double)yj * log((double)acc) : 0.0) - (double)acc;
       }
     }
@@ -179,18 +184,29 @@ __global__ void __launch_bounds__(kSpmvThreads) csc_back_kernel(const uint32_t *
   const int64_t gid = ((int64_t)blockIdx.x * kSpmvThreads + threadIdx.x) / G;
   const int sub = threadIdx.x & (G - 1);
   uint32_t b = 0, e = 0;
-  if (gid < n) { b = col_ptr[gid]; e = col_ptr[gid + 1]; }
+  // the epilogue's loads are issued with the pointers, ahead of the gathers
+  float is = 0.0f, xv = 0.0f, in = 0.0f;
+  if (gid < n) {
+    b = col_ptr[gid];
+    e = col_ptr[gid + 1];
+    if (sub == 0) {
+      in = inv_n[gid];
+      if (MODE != 0) {
+        is = inv_colsum[gid];
+        xv = x[gid];
+      }
+    }
+  }
   float acc = segment_dot<V, G>(b, e, row, val, r, sub);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
   if (gid < n && sub == 0) {
     if (MODE == 0) {
-      x[gid] = acc * inv_n[gid];
+      x[gid] = acc * in;
     } else {
-      const float is = inv_colsum[gid];
-      const float xn = is > 0.0f ? x[gid] * acc * is : (MODE == 3 ? x[gid] : 0.0f);
+      const float xn = is > 0.0f ? xv * acc * is : (MODE == 3 ? xv : 0.0f);
       x[gid] = xn;
-      xs[gid] = xn * inv_n[gid];
+      xs[gid] = xn * in;
     }
   }
 }
