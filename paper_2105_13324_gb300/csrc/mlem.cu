@@ -1371,6 +1371,7 @@ __global__ void __launch_bounds__(kStreamThreads) batch_forward_kernel(const Bat
                                                                     int n_sys) {
   __shared__ float s_prod[kStreamTile];
   __shared__ BatchSys s_desc;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   batch_forward_tile(systems, tile_off, n_sys, blockIdx.x, s_prod, &s_desc);
 }
 
@@ -1378,6 +1379,7 @@ __global__ void __launch_bounds__(kStreamThreads) batch_back_kernel(const BatchS
                                                                  const uint64_t *__restrict__ tile_off, int n_sys) {
   __shared__ float s_prod[kStreamTile];
   __shared__ BatchSys s_desc;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   batch_back_tile(systems, tile_off, n_sys, blockIdx.x, s_prod, &s_desc);
 }
 
@@ -1711,11 +1713,11 @@ static int batch_enqueue(mc_batch *b, int n_iter, cudaStream_t s) {
   for (int it = 0; it < n_iter; ++it) {
     if (b->n_tiles_fwd) {
       count_launch();
-      batch_forward_kernel<<<(unsigned)b->n_tiles_fwd, kStreamThreads, 0, s>>>(sys, b->tile_fwd.as<uint64_t>(), b->n);
+      launch_pdl(batch_forward_kernel, (unsigned)b->n_tiles_fwd, kStreamThreads, s, sys, b->tile_fwd.as<uint64_t>(), b->n);
     }
     if (b->n_tiles_bwd) {
       count_launch();
-      batch_back_kernel<<<(unsigned)b->n_tiles_bwd, kStreamThreads, 0, s>>>(sys, b->tile_bwd.as<uint64_t>(), b->n);
+      launch_pdl(batch_back_kernel, (unsigned)b->n_tiles_bwd, kStreamThreads, s, sys, b->tile_bwd.as<uint64_t>(), b->n);
     }
   }
   count_launch();
