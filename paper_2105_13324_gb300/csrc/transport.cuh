@@ -58,6 +58,8 @@ template <typename T> struct TArgs {
   T start_deg, inv_delta, psi_views;  // azimuth window of candidate views
   int views_per_turn;                 // 360 / delta if integral, else 0
   int t_coll, t_emit;                 // lanes that must wait before a warp runs collisions / emissions
+  uint64_t stride;                    // threads in the grid
+  uint32_t step_v[3];                 // stride mod N as a voxel step (x, y, z)
   int primary_only;                   // tally only photons that never scattered
   T sigma, plane, bin, half_bu, half_bv;
   int n_views, bins_u, bins_v;
@@ -546,18 +548,26 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
     for (int i = threadIdx.x; i < kSigTab; i += blockDim.x) s_sig[i] = a.sig_tab[i];
   if (threadIdx.x < 4) s_fates[threadIdx.x] = 0ull;
   __syncthreads();
+  // the emission energy's cross-section quantities, once per block
+  __shared__ T s_en0[4];
+  if (threadIdx.x == 0) {
+    Energy<T> e0;
+    e0.e = e0.sig = e0.e3 = e0.ie3 = (T)0;
+    e0.set(a.e0, a, s_sig);
+    s_en0[0] = e0.e; s_en0[1] = e0.sig; s_en0[2] = e0.e3; s_en0[3] = e0.ie3;
+  }
+  __syncthreads();
 
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t stride = a.stride;
   // voxel of the next history, kept as (vi, vj, vk) and advanced by the
   // stride (mod N) with carries
   const uint32_t nx = (uint32_t)a.nx, ny = (uint32_t)a.ny, nz = (uint32_t)a.nz;
-  uint32_t vi, vj, vk, si, sj, sk;
+  uint32_t vi, vj, vk;
+  const uint32_t si = a.step_v[0], sj = a.step_v[1], sk = a.step_v[2];
   {
     const uint32_t v0 = (uint32_t)((a.first + tid) % a.n_vox);
     vi = v0 % nx; vj = (v0 / nx) % ny; vk = v0 / (nx * ny);
-    const uint32_t sm = (uint32_t)(stride % a.n_vox);
-    si = sm % nx; sj = (sm / nx) % ny; sk = sm / (nx * ny);
   }
   uint64_t i = tid;
 
@@ -569,8 +579,6 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
   T px = 0, py = 0, pz = 0, dx = 0, dy = 0, dz = 1;
   Energy<T> en;
   en.e = en.sig = en.e3 = en.ie3 = (T)0;
-  Energy<T> en0;
-  en0.set(a.e0, a, s_sig);
   uint32_t steps = 0, n_virtual = 0, n_real = 0, n_compton = 0;
   uint64_t cur_i = 0;
   uint32_t n_fate[4] = {0u, 0u, 0u, 0u};  // fates of this thread's histories
@@ -656,7 +664,7 @@ __global__ void __launch_bounds__(kRingThreads) transport_kernel(const __grid_co
       dx = sth * cph;
       dy = sth * sph;
       dz = ct;
-      en = en0;
+      en.e = s_en0[0]; en.sig = s_en0[1]; en.e3 = s_en0[2]; en.ie3 = s_en0[3];
       steps = n_virtual = n_real = n_compton = 0;
       st = S_FLY;
       if (FD) push_fd<T>(a, a.first + cur_i, 0u, px, py, pz, dx, dy, dz, en.e, (T)1);
@@ -1238,6 +1246,13 @@ template <typename T> int launch_transport_t(const TransportSetup &ts, cudaStrea
   const int64_t full = (int64_t)device_sm_count() * per_sm;
   const int64_t need = (int64_t)((ts.count + threads - 1) / threads);
   const int grid = (int)(need < full ? need : full);
+  a.stride = (uint64_t)grid * threads;
+  {
+    const uint32_t sm = (uint32_t)(a.stride % a.n_vox);
+    a.step_v[0] = sm % (uint32_t)ts.nx;
+    a.step_v[1] = (sm / (uint32_t)ts.nx) % (uint32_t)ts.ny;
+    a.step_v[2] = sm / ((uint32_t)ts.nx * (uint32_t)ts.ny);
+  }
   if (ts.forced) { count_launch(); transport_kernel<T, false, true><<<grid, threads, 0, s>>>(a); }
   else if (ts.records) { count_launch(); transport_kernel<T, true><<<grid, threads, 0, s>>>(a); }
   else { count_launch(); transport_kernel<T, false><<<grid, threads, 0, s>>>(a); }
