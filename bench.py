@@ -51,12 +51,12 @@ OPS_PER_EMISSION = 30.0
 ALU_LANES_PER_SM = 128
 # DRAM bytes (read + write) counted by ncu for the present kernels, for the
 # `traffic` fields: transport_kernel<float> in one launch of 1e9 histories of
-# the 128^3 torso (13.52 MB + 987.50 MB: mostly the escape queue, which a
+# the 128^3 torso (13.38 MB + 987.47 MB: mostly the escape queue, which a
 # launch of 1e8 histories keeps in L2), per history; and one ML-EM iteration's
 # forward + back-projection warp-chunk kernels on the benchmark's 1e9-history
 # matrix (82.28 + 0.43 MB and 99.64 + 3.52 MB, single-pass capture).  To be
 # taken again (or set to None) whenever those kernels change.
-TRANSPORT_DRAM_BYTES_PER_HISTORY = (13516544 + 987495168) / 1e9
+TRANSPORT_DRAM_BYTES_PER_HISTORY = (13383168 + 987473664) / 1e9
 MLEM_DRAM_BYTES_PER_ITER_1E9 = 82282496 + 432896 + 99639552 + 3522560
 
 
